@@ -1,0 +1,243 @@
+/*
+ * ata.h -- C ABI of the GB300 library for the symmetric product C = A^t A.
+ *
+ * The operation is the one of Arrigoni & Massini, "Fast Strassen-based A^t A
+ * Parallel Multiplication" (arXiv 1902.02104), Section 3, Algorithm 1:
+ *
+ *   input  A, a real m x n matrix (Algorithm 1, "Input");
+ *   output one triangle of C = A^t A (Algorithm 1, "Output"; Section 3 keeps
+ *          n(n+1)/2 entries because C is symmetric).
+ *
+ * The library computes it with the ATA recursion: the 2 x 2 block split of
+ * Section 3 (Eq. "submatrices", ceil/floor halves), the block formulas of
+ * Eq. "Cij" (diagonal blocks by recursion, the off-diagonal block by
+ * Strassen products, Section 4.2.2), and the base case of Algorithm 1 with
+ * the cutoff as a parameter.  C_21 is never computed: the library returns
+ * C_12 = C_21^t, i.e. the upper triangle.
+ *
+ * Layouts
+ *   A         row-major, m rows, n columns, leading dimension lda >= n
+ *             (elements).  Element (k, i) is at A[k*lda + i].  FP64 for
+ *             ATA_F64 and ATA_F64_OZAKI, FP32 for the FP32 modes.  Device
+ *             memory for ata_execute / ata_execute_batched; host memory for
+ *             ata_execute_host.  Never modified.
+ *   C_packed  FP64, n(n+1)/2 entries, row-major packed upper triangle:
+ *             C(i, j), i <= j, is at i*n - i*(i-1)/2 + (j - i).  This is the
+ *             same memory order as LAPACK's column-major packed lower
+ *             triangle ('L'), i.e. the paper's lower triangle read by
+ *             columns.  Every entry is written (m == 0 writes zeros).
+ *
+ * Ownership
+ *   The caller owns A and C_packed.  A plan owns its device workspace, its
+ *   task tables and its CUDA graph; ata_plan_destroy frees them.  A plan
+ *   runs one execution at a time (its workspace is reused); run
+ *   independent products concurrently with separate plans.
+ *
+ * Errors
+ *   Arguments are checked before any work is queued; a bad argument returns
+ *   ATA_EINVAL and queues nothing.  Execution is asynchronous on the given
+ *   stream: an error raised by the device surfaces as ATA_ECUDA from a later
+ *   call on the same plan (or from ata_poll).  NaN and Inf in A propagate by
+ *   IEEE rules; they are not checked.  ata_last_error_message() returns a
+ *   thread-local description of the last failure.
+ */
+#ifndef ATA_H
+#define ATA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ATA_OK = 0,
+    ATA_EINVAL = 1,        /* bad argument; nothing was queued            */
+    ATA_ENOMEM = 2,        /* device or host allocation failed            */
+    ATA_EUNSUPPORTED = 3,  /* valid request this build cannot run         */
+    ATA_ECUDA = 4,         /* CUDA runtime / device error                 */
+    ATA_PENDING = 5,       /* ata_poll: request still running             */
+    ATA_ETIMEOUT = 6,      /* ata_poll / ata_server_wait: time limit hit  */
+    ATA_EBUSY = 7          /* admission refused: no slot or budget free   */
+} ata_status;
+
+/* Input type and leaf arithmetic. */
+typedef enum {
+    ATA_F64 = 0,           /* FP64 input, FP64 leaves (DFMA), FP64 sums       */
+    ATA_F32_BF16X3 = 1,    /* FP32 input, leaves on bf16 tensor cores with a
+                              3-way split of each operand, FP32 accumulation
+                              in chunks added into FP64                      */
+    ATA_F32_TF32 = 2,      /* FP32 input, TF32 tensor-core leaves, FP32
+                              accumulation in chunks added into FP64          */
+    ATA_F64_OZAKI = 3      /* FP64 input, FP64-accuracy leaves emulated on
+                              bf16 tensor cores (exact slice products, FP64
+                              Strassen sums and final accumulation)          */
+} ata_dtype;
+
+/* Strassen form used for the off-diagonal products. */
+typedef enum {
+    ATA_STRASSEN = 0,      /* Strassen 1969, the form of Section 4.2.2        */
+    ATA_WINOGRAD = 1       /* Winograd's variant (Section 1)                  */
+} ata_variant;
+
+typedef struct ata_plan_s* ata_plan;
+
+/* Planner statistics (host-only; see ata_plan_query). */
+typedef struct {
+    int64_t m, n;
+    int32_t dtype, cutoff;      /* cutoff actually used                    */
+    int32_t depth;              /* levels of the ATA column recursion      */
+    int32_t n_diag_leaves;      /* base-case (diagonal) blocks             */
+    int32_t n_nodes;            /* off-diagonal products C_12, one per node*/
+    int32_t max_strassen_levels;
+    int32_t n_leaf_products;    /* products run by the leaf kernel         */
+    int32_t n_leaf_tiles;       /* output tiles of the leaf launch          */
+    int32_t n_sum_tasks;        /* materialised Strassen operand sums       */
+    int32_t n_combine_tasks;    /* Strassen output combines                 */
+    int32_t n_launches;         /* kernels per execution                    */
+    int64_t mults;              /* scalar multiplications of the tree (on
+                                   padded sizes; Section 3.1 recurrence)    */
+    int64_t classical_mults;    /* m * n (n + 1) / 2                        */
+    int64_t adds;               /* scalar additions of Strassen sums/combines*/
+    int64_t workspace_bytes;    /* device workspace the plan allocates      */
+} ata_plan_info;
+
+/* Status text ("ATA_OK", ...).  Never NULL. */
+const char* ata_status_string(ata_status s);
+
+/* Thread-local description of the last failure in this thread. */
+const char* ata_last_error_message(void);
+
+/* Run the planner only (no device call): fills *out for the plan that
+ * ata_plan_create(m, n, dtype, cutoff) would build.  cutoff must be in
+ * [16, 4096]; 0 selects it by the planner's cost model (as ata_plan_create).
+ * Errors: ATA_EINVAL for m < 0, n < 0, a bad dtype or cutoff, n > 2^31-1. */
+ata_status ata_plan_query(int64_t m, int64_t n, ata_dtype dtype, int cutoff,
+                          ata_plan_info* out);
+
+/* Build a plan for an m x n input: the recursion tree of Algorithm 1 (base
+ * case min(rows, cols) <= cutoff), the Strassen products of every
+ * off-diagonal block, the task tables, and the device workspace (allocated
+ * here, on the current device).  cutoff in [16, 4096]; 0 = autotune: the
+ * cutoff minimising the planner's cost model of this part (leaf
+ * multiply-adds, Strassen additions and workspace traffic at the measured
+ * rates, workspace capped at 48 GiB), cached per shape and dtype.
+ * Errors: ATA_EINVAL (bad sizes, dtype or cutoff, NULL out), ATA_ENOMEM,
+ * ATA_ECUDA. */
+ata_status ata_plan_create(ata_plan* out, int64_t m, int64_t n,
+                           ata_dtype dtype, int cutoff);
+
+/* Planner options beyond the cutoff.  Fields set to -1 take the default. */
+typedef struct {
+    int32_t cutoff;              /* as in ata_plan_create (0 = autotune)      */
+    int32_t variant;             /* ata_variant (-1 = ATA_STRASSEN)            */
+    int32_t fuse_levels;         /* bottom Strassen levels whose operand sums
+                                    are formed inside the leaf loads instead of
+                                    materialised (-1 = dtype default: 0 for
+                                    the FP64 modes, 1 for the FP32 modes)      */
+    int32_t max_strassen_levels; /* cap on Strassen levels per product
+                                    (-1 = none; 0 = classical products)        */
+} ata_plan_options;
+
+/* Same as ata_plan_create with explicit options (opts may not be NULL).
+ * Errors: as ata_plan_create; ATA_EUNSUPPORTED if the fused operands would
+ * exceed the kernels' 32 terms per operand. */
+ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n,
+                                ata_dtype dtype, const ata_plan_options* opts);
+
+/* ata_plan_query with explicit options. */
+ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype,
+                               const ata_plan_options* opts,
+                               ata_plan_info* out);
+
+/* Statistics of a created plan. */
+ata_status ata_plan_get_info(ata_plan plan, ata_plan_info* out);
+
+/* Device workspace held by the plan, in bytes. */
+ata_status ata_plan_workspace_size(ata_plan plan, size_t* bytes);
+
+/* C_packed = A^t A, queued on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  A and C_packed are device pointers (layouts above).
+ * The first call on a plan captures its CUDA graph; later calls replay it.
+ * Returns once the work is queued.
+ * Errors: ATA_EINVAL (NULL plan, lda < n, NULL A with m*n > 0, NULL
+ * C_packed with n > 0, A or C_packed not 8-byte aligned), ATA_ECUDA. */
+ata_status ata_execute(ata_plan plan, const void* A, int64_t lda,
+                       double* C_packed, void* stream);
+
+/* End-to-end convenience: A and C_packed in HOST memory.  Copies A to the
+ * device, runs ata_execute on `stream`, copies C back and waits for the
+ * stream.  Device staging buffers are owned by the plan (allocated on first
+ * use).  Errors: as ata_execute, plus ATA_ENOMEM. */
+ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda,
+                            double* C_packed_host, void* stream);
+
+/* Many independent products in one queued batch: plans[i] (each built for
+ * its own m_i x n_i and dtype) applied to A[i] (device, leading dimension
+ * lda[i]) into C_packed[i].  All leaf tiles of all instances run in one
+ * persistent launch, heaviest first; sums and combines are grouped per
+ * level across instances.  Plans may not repeat within one call.
+ * Errors: ATA_EINVAL (count < 0, NULL arrays, a repeated plan, mixed dtype
+ * families), ATA_ENOMEM, ATA_ECUDA. */
+ata_status ata_execute_batched(const ata_plan* plans, int count,
+                               const void* const* A, const int64_t* lda,
+                               double* const* C_packed, void* stream);
+
+/* Stage timing.  With enable != 0 the plan's graph also records CUDA events
+ * on the execution stream before the operand-split launches, before and
+ * after the leaf launch, and after the combine launches (the graph is
+ * re-captured on the next ata_execute).  ata_plan_stage_times returns, for
+ * the most recent execution (which must have completed), the milliseconds
+ * of the split launches, the leaf launch and the combine launches.
+ * Errors: ATA_EINVAL (NULL arguments, timing not enabled, no execution yet),
+ * ATA_ECUDA. */
+ata_status ata_plan_enable_stage_timing(ata_plan plan, int enable);
+ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms,
+                                float* combine_ms);
+
+/* Release the plan (waits for its queued work first). */
+void ata_plan_destroy(ata_plan plan);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of independent requests.               */
+/* ------------------------------------------------------------------ */
+
+typedef struct ata_server_s* ata_server;
+typedef uint64_t ata_ticket;
+
+/* Start a server on the current device: a host scheduler thread, up to
+ * max_inflight concurrent requests on their own streams, and a device-memory
+ * budget (bytes) that bounds the plans' workspaces and staging buffers held
+ * at once.  Plans are created on first use of a shape and stay resident
+ * while the budget allows.  Errors: ATA_EINVAL, ATA_ENOMEM, ATA_ECUDA. */
+ata_status ata_server_create(ata_server* out, size_t device_budget_bytes,
+                             ata_dtype dtype, int max_inflight);
+
+/* Submit one request: A (device pointer, m x n, lda) -> C_packed (device).
+ * The buffers must stay valid until the ticket completes.  Returns at once
+ * with a ticket; the request is admitted when a slot and budget bytes are
+ * free.  Errors: ATA_EINVAL (bad sizes or pointers), ATA_EBUSY (the request
+ * alone exceeds the budget). */
+ata_status ata_submit(ata_server srv, int64_t m, int64_t n, const void* A,
+                      int64_t lda, double* C_packed, ata_ticket* ticket);
+
+/* Completion check.  timeout_us = 0 polls once; > 0 waits up to that long.
+ * Returns ATA_OK (done; the ticket is released), ATA_PENDING (timeout_us ==
+ * 0 and not done), ATA_ETIMEOUT (waited and not done), ATA_EINVAL (unknown
+ * ticket), or the request's own error. */
+ata_status ata_poll(ata_server srv, ata_ticket ticket, int timeout_us);
+
+/* Latency statistics of completed requests (submit to completion seen by
+ * the scheduler), in microseconds, and the count. */
+ata_status ata_server_stats(ata_server srv, double* p50_us, double* p99_us,
+                            int64_t* completed);
+
+/* Stop the scheduler after draining queued work, then free everything. */
+void ata_server_destroy(ata_server srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATA_H */

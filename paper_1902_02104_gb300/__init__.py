@@ -1,0 +1,308 @@
+"""Python binding of the C ABI in ``include/ata.h`` (argument marshalling only).
+
+Every step of C = A^t A runs in the CUDA library ``_lib/libata.so``; this
+module only converts torch tensors / numpy arrays into pointers, sizes and a
+stream handle.  PyTorch supplies device memory and streams.  If the library
+is missing the import fails: there is no other code path.
+
+Functions keep the C names (``ata_plan_create``, ``ata_execute``, ...); the
+:class:`Plan` and :class:`Server` classes wrap the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "ATA_F64", "ATA_F32_BF16X3", "ATA_F32_TF32", "ATA_F64_OZAKI", "ATA_STRASSEN", "ATA_WINOGRAD",
+    "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
+    "ata_execute_batched", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
+    "packed_size", "lib_path",
+]
+
+ATA_F64, ATA_F32_BF16X3, ATA_F32_TF32, ATA_F64_OZAKI = 0, 1, 2, 3
+ATA_STRASSEN, ATA_WINOGRAD = 0, 1
+ATA_OK, ATA_EINVAL, ATA_ENOMEM, ATA_EUNSUPPORTED, ATA_ECUDA, ATA_PENDING, ATA_ETIMEOUT, ATA_EBUSY = range(8)
+_STATUS = ["ATA_OK", "ATA_EINVAL", "ATA_ENOMEM", "ATA_EUNSUPPORTED", "ATA_ECUDA", "ATA_PENDING",
+           "ATA_ETIMEOUT", "ATA_EBUSY"]
+DTYPE_NAMES = {"f64": ATA_F64, "bf16x3": ATA_F32_BF16X3, "tf32": ATA_F32_TF32, "ozaki": ATA_F64_OZAKI}
+
+
+class AtaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{_STATUS[status] if 0 <= status < len(_STATUS) else status}: {msg}")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("cutoff", ctypes.c_int32), ("depth", ctypes.c_int32), ("n_diag_leaves", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int32), ("max_strassen_levels", ctypes.c_int32),
+                ("n_leaf_products", ctypes.c_int32), ("n_leaf_tiles", ctypes.c_int32),
+                ("n_sum_tasks", ctypes.c_int32), ("n_combine_tasks", ctypes.c_int32),
+                ("n_launches", ctypes.c_int32), ("mults", ctypes.c_int64), ("classical_mults", ctypes.c_int64),
+                ("adds", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("cutoff", ctypes.c_int32), ("variant", ctypes.c_int32), ("fuse_levels", ctypes.c_int32),
+                ("max_strassen_levels", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load ``libata.so`` (building it first when sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or os.environ.get("ATA_AUTOBUILD", "1") == "1":
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    i64, i32, vp, dp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p
+    sig = {
+        "ata_status_string": ([i32], ctypes.c_char_p),
+        "ata_last_error_message": ([], ctypes.c_char_p),
+        "ata_plan_query": ([i64, i64, i32, i32, ctypes.POINTER(PlanInfo)], i32),
+        "ata_plan_query_opts": ([i64, i64, i32, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanInfo)], i32),
+        "ata_plan_create": ([ctypes.POINTER(vp), i64, i64, i32, i32], i32),
+        "ata_plan_create_opts": ([ctypes.POINTER(vp), i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
+        "ata_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i32),
+        "ata_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "ata_execute": ([vp, vp, i64, dp, vp], i32),
+        "ata_execute_host": ([vp, vp, i64, dp, vp], i32),
+        "ata_execute_batched": ([ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                 ctypes.POINTER(vp), vp], i32),
+        "ata_plan_destroy": ([vp], None),
+        "ata_plan_enable_stage_timing": ([vp, i32], i32),
+        "ata_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_float)], i32),
+        "ata_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i32, i32], i32),
+        "ata_submit": ([vp, i64, i64, vp, i64, dp, ctypes.POINTER(ctypes.c_uint64)], i32),
+        "ata_poll": ([vp, ctypes.c_uint64, i32], i32),
+        "ata_server_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(i64)], i32),
+        "ata_server_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != ATA_OK:
+        raise AtaError(st, load().ata_last_error_message().decode(errors="replace"))
+
+
+def packed_size(n: int) -> int:
+    return n * (n + 1) // 2
+
+
+def _dtype_code(dtype) -> int:
+    if isinstance(dtype, str):
+        return DTYPE_NAMES[dtype]
+    return int(dtype)
+
+
+def _opts(cutoff=0, variant=-1, fuse_levels=-1, max_strassen_levels=-1) -> PlanOptions:
+    return PlanOptions(int(cutoff), int(variant), int(fuse_levels), int(max_strassen_levels))
+
+
+def ata_plan_query(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> dict:
+    """Planner statistics for (m, n, dtype, cutoff) without touching a GPU."""
+    info = PlanInfo()
+    o = _opts(cutoff, **opts)
+    _check(load().ata_plan_query_opts(m, n, _dtype_code(dtype), ctypes.byref(o), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A plan handle: ``Plan(m, n, dtype, cutoff)`` then ``plan(A, C)``."""
+
+    def __init__(self, m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts):
+        self.m, self.n, self.dtype = int(m), int(n), _dtype_code(dtype)
+        h = ctypes.c_void_p()
+        o = _opts(cutoff, **opts)
+        _check(load().ata_plan_create_opts(ctypes.byref(h), self.m, self.n, self.dtype, ctypes.byref(o)))
+        self.handle = h
+
+    @property
+    def info(self) -> dict:
+        info = PlanInfo()
+        _check(load().ata_plan_get_info(self.handle, ctypes.byref(info)))
+        return info.as_dict()
+
+    @property
+    def in_dtype(self):
+        import torch
+        return torch.float64 if self.dtype in (ATA_F64, ATA_F64_OZAKI) else torch.float32
+
+    def enable_stage_timing(self, enable: bool = True):
+        _check(load().ata_plan_enable_stage_timing(self.handle, int(enable)))
+
+    def stage_times(self) -> dict:
+        """Milliseconds of the split, leaf and combine stages of the last
+        (completed) execution; needs enable_stage_timing()."""
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        _check(load().ata_plan_stage_times(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"split_ms": a.value, "leaf_ms": b.value, "combine_ms": c.value}
+
+    def __call__(self, A, C=None, stream=None):
+        return ata_execute(self, A, C, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ata_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ata_plan_create(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> Plan:
+    return Plan(m, n, dtype, cutoff, **opts)
+
+
+def ata_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def _check_A(plan: Plan, A):
+    import torch
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if A.dtype != plan.in_dtype:
+        raise TypeError(f"A must be {plan.in_dtype} for this plan")
+    if A.dim() != 2 or tuple(A.shape) != (plan.m, plan.n):
+        raise ValueError(f"A must be {plan.m} x {plan.n}")
+    if plan.m > 0 and plan.n > 0 and A.stride(1) != 1:
+        raise ValueError("A must be row-major (unit column stride)")
+    return max(A.stride(0), plan.n, 1) if plan.m > 1 else max(plan.n, 1)
+
+
+def ata_execute(plan: Plan, A, C=None, stream=None):
+    """C_packed = A^t A on the GPU; A (m x n, row-major CUDA tensor) and the
+    packed FP64 output C (allocated when None).  Asynchronous on `stream`."""
+    import torch
+    lda = _check_A(plan, A)
+    if C is None:
+        C = torch.empty(packed_size(plan.n), dtype=torch.float64, device=A.device)
+    if C.dtype != torch.float64 or C.numel() != packed_size(plan.n) or not C.is_contiguous():
+        raise ValueError("C must be a contiguous float64 tensor of n(n+1)/2 entries")
+    _check(load().ata_execute(plan.handle, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(C.data_ptr()),
+                              _stream_handle(stream)))
+    return C
+
+
+def ata_execute_host(plan: Plan, A, C=None, stream=None):
+    """End to end from host memory (numpy array or CPU tensor, pinned or not)."""
+    import numpy as np
+    A_np = A.numpy() if hasattr(A, "numpy") and not isinstance(A, np.ndarray) else A
+    want = np.float64 if plan.dtype in (ATA_F64, ATA_F64_OZAKI) else np.float32
+    if A_np.dtype != want or A_np.shape != (plan.m, plan.n) or not A_np.flags.c_contiguous:
+        raise ValueError(f"A must be a C-contiguous {want.__name__} array of shape ({plan.m}, {plan.n})")
+    if C is None:
+        C = np.empty(packed_size(plan.n), dtype=np.float64)
+    C_np = C.numpy() if hasattr(C, "numpy") and not isinstance(C, np.ndarray) else C
+    if C_np.dtype != np.float64 or C_np.size != packed_size(plan.n) or not C_np.flags.c_contiguous:
+        raise ValueError("C must be a contiguous float64 array of n(n+1)/2 entries")
+    _check(load().ata_execute_host(plan.handle, ctypes.c_void_p(A_np.ctypes.data), max(plan.n, 1),
+                                   ctypes.c_void_p(C_np.ctypes.data), _stream_handle(stream)))
+    return C
+
+
+def ata_execute_batched(plans, As, Cs=None, stream=None):
+    """Run many plans in one queued batch (one persistent leaf launch)."""
+    import torch
+    count = len(plans)
+    if Cs is None:
+        Cs = [torch.empty(packed_size(p.n), dtype=torch.float64, device=A.device) for p, A in zip(plans, As)]
+    ph = (ctypes.c_void_p * count)(*[p.handle for p in plans])
+    ap = (ctypes.c_void_p * count)(*[A.data_ptr() for A in As])
+    ld = (ctypes.c_int64 * count)(*[_check_A(p, A) for p, A in zip(plans, As)])
+    cp = (ctypes.c_void_p * count)(*[C.data_ptr() for C in Cs])
+    _check(load().ata_execute_batched(ph, count, ap, ld, cp, _stream_handle(stream)))
+    return Cs
+
+
+class Server:
+    """Continuous-batching server (``ata_server_create`` / ``ata_submit`` / ``ata_poll``)."""
+
+    def __init__(self, budget_bytes: int, dtype=ATA_F32_BF16X3, max_inflight: int = 8):
+        h = ctypes.c_void_p()
+        _check(load().ata_server_create(ctypes.byref(h), int(budget_bytes), _dtype_code(dtype), int(max_inflight)))
+        self.handle = h
+        self.dtype = _dtype_code(dtype)
+        self._keep = {}
+
+    def submit(self, A, C) -> int:
+        t = ctypes.c_uint64()
+        m, n = A.shape
+        _check(load().ata_submit(self.handle, m, n, ctypes.c_void_p(A.data_ptr()), max(A.stride(0), n, 1),
+                                 ctypes.c_void_p(C.data_ptr()), ctypes.byref(t)))
+        self._keep[t.value] = (A, C)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0) -> int:
+        st = load().ata_poll(self.handle, ticket, int(timeout_us))
+        if st == ATA_OK:
+            self._keep.pop(ticket, None)
+        elif st not in (ATA_PENDING, ATA_ETIMEOUT):
+            self._keep.pop(ticket, None)
+            _check(st)
+        return st
+
+    def stats(self) -> dict:
+        p50, p99, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(load().ata_server_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n)))
+        return {"p50_us": p50.value, "p99_us": p99.value, "completed": n.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ata_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ata_server_create(budget_bytes: int, dtype=ATA_F32_BF16X3, max_inflight: int = 8) -> Server:
+    return Server(budget_bytes, dtype, max_inflight)
+
+
+def ata_submit(server: Server, A, C) -> int:
+    return server.submit(A, C)
+
+
+def ata_poll(server: Server, ticket: int, timeout_us: int = 0) -> int:
+    return server.poll(ticket, timeout_us)

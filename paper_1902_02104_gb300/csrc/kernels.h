@@ -1,0 +1,56 @@
+// kernels.h -- launch interface of the device kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace ata {
+
+// Device pointers an execution binds: the caller's A and C and the plan's
+// workspace, per instance.  Kernels receive a BindSet by value (a
+// __grid_constant__ parameter), so a launch snapshots its pointers and a
+// captured graph is re-pointed by updating kernel-node parameters.
+struct Bind {
+    const void* A;
+    double* C;
+    char* W;
+    int64_t n;
+};
+
+constexpr int kMaxBatchBind = 512;  // instances per batched launch (16 KB of parameters)
+
+template <int NB>
+struct BindSet {
+    Bind b[NB];
+};
+
+// One output tile of the leaf launch.
+struct LeafTile {
+    int32_t prod;
+    int32_t ti, tj;
+};
+
+// A range of rows of an elementwise task (split or combine).
+struct Chunk {
+    int32_t task;
+    int32_t row0, nrows;
+};
+
+constexpr int kF64Tile = 64;      // FP64 leaf tile (rows and columns)
+constexpr int kMaxTerms = 32;     // terms per operand the leaf kernels accept
+
+// `binds` holds nb <= kMaxBatchBind instances (nb == 1 uses the single-plan
+// instantiation of each kernel).
+cudaError_t launch_leaf_f64(const Bind* binds, int nb, const LeafProduct* prods, const Term* terms, const LeafTile* tiles,
+                            int ntiles, int* counter, int grid, cudaStream_t s);
+
+cudaError_t launch_split(const Bind* binds, int nb, const SplitTask* tasks, const Chunk* chunks, int nchunks, int8_t src_dt,
+                         int8_t dst_dt, cudaStream_t s);
+
+cudaError_t launch_combine(const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks, int nchunks,
+                           cudaStream_t s);
+
+// Resident blocks of the FP64 leaf kernel per SM (for persistent grids).
+int leaf_f64_blocks_per_sm();
+
+}  // namespace ata

@@ -1,0 +1,329 @@
+// kernels_f64.cu -- FP64 leaf products, Strassen operand splits and output
+// combines.
+//
+// On GB300 the FP64 pipe issues about two DFMA per clock per SM (measured
+// 1.20 TFLOP/s on 152 SMs; DMMA is slower, 1.05 TFLOP/s), so the FP64 leaf
+// is a SIMT DFMA kernel and is bound by that pipe: a 64 x 64 tile with a K
+// slab of 16 takes ~32k clocks of DFMA per block while its 16 KB of operand
+// loads take a few hundred, so no load pipelining is needed.  What matters is
+// not issuing DFMAs on padding: work is skipped at 8 x 8 granularity (warp-
+// uniform branches) outside the valid extent and below the diagonal of
+// symmetric (SYRK) tiles.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace ata {
+namespace {
+
+__device__ __forceinline__ int64_t packed_start(int64_t i, int64_t n) { return i * n - i * (i - 1) / 2; }
+
+template <typename T>
+__device__ __forceinline__ const T* term_ptr(const Bind& b, const Term& t) {
+    // b is the instance of the term (t.inst)
+    const T* base = t.buf == BUF_A ? reinterpret_cast<const T*>(b.A) : reinterpret_cast<const T*>(b.W);
+    return base + t.off;
+}
+
+// Value of a fused operand (sum of signed terms) at (k, c); zero outside
+// each term's valid extent (implicit zero padding of uneven blocks).
+template <int NB>
+__device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* ts, int nt, int k, int c) {
+    double v = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        const Term& tm = ts[t];
+        if (k < tm.rows && c < tm.cols) {
+            const double x = __ldg(term_ptr<double>(bs.b[tm.inst], tm) + (int64_t)k * tm.ld + c);
+            v = tm.neg ? v - x : v + x;
+        }
+    }
+    return v;
+}
+
+constexpr int TILE = kF64Tile;  // 64
+constexpr int BK = 16;
+constexpr int NTHREADS = 256;
+
+// Persistent leaf kernel: blocks pull tiles (heaviest first) from a counter.
+// out(p x r) = X^t Y where X (K x p) and Y (K x r) are term sums.  Each warp
+// owns 8 tile rows; lane (lr, lc) owns rows 2lr, 2lr+1 of that strip and
+// columns lc + 8b, b = 0..7.  Accumulation runs k ascending per entry.
+template <int NB>
+__global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                            const LeafProduct* __restrict__ prods,
+                                                            const Term* __restrict__ terms,
+                                                            const LeafTile* __restrict__ tiles, int ntiles,
+                                                            int* __restrict__ counter) {
+    __shared__ double Xs[BK][TILE];
+    __shared__ double Ys[BK][TILE];
+    __shared__ Term sx[kMaxTerms], sy[kMaxTerms];
+    __shared__ int s_tile;
+    __shared__ LeafProduct sp;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int lr = lane >> 3, lc = lane & 7;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const LeafTile lt = tiles[t];
+        if (tid == 0) sp = prods[lt.prod];
+        __syncthreads();
+        const int nx = sp.nx, ny = sp.ny;
+        if (tid < nx) sx[tid] = terms[sp.x0 + tid];
+        if (tid >= 64 && tid - 64 < ny) sy[tid - 64] = terms[sp.y0 + tid - 64];
+        const int i0 = lt.ti * TILE, j0 = lt.tj * TILE;
+        const int rows_v = min(TILE, sp.out_rows - i0);
+        const int cols_v = min(TILE, sp.out_cols - j0);
+        const bool diag = sp.out_kind == OUT_SYRK && lt.ti == lt.tj;
+        const int K = sp.K;
+        __syncthreads();
+
+        const bool warp_rows = warp * 8 < rows_v;
+        bool bval[8];
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb)
+            bval[bb] = warp_rows && (8 * bb < cols_v) && (!diag || 8 * bb + 7 >= warp * 8);
+
+        double acc[2][8];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 8; ++bb) acc[a][bb] = 0.0;
+
+        for (int k0 = 0; k0 < K; k0 += BK) {
+            // stage the fused operand slabs (BK x 64 each); columns are contiguous in memory
+#pragma unroll
+            for (int e = 0; e < (BK * TILE) / NTHREADS; ++e) {
+                const int idx = tid + e * NTHREADS;
+                const int kk = idx / TILE, c = idx % TILE;
+                const int k = k0 + kk;
+                Xs[kk][c] = (k < K) ? operand_at(bs, sx, nx, k, i0 + c) : 0.0;
+                Ys[kk][c] = (k < K) ? operand_at(bs, sy, ny, k, j0 + c) : 0.0;
+            }
+            __syncthreads();
+            if (warp_rows) {
+                const int kmax = min(BK, K - k0);
+                const int row = warp * 8 + 2 * lr;
+                for (int kk = 0; kk < kmax; ++kk) {
+                    const double xa = Xs[kk][row], xb = Xs[kk][row + 1];
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        if (bval[bb]) {
+                            const double y = Ys[kk][lc + 8 * bb];
+                            acc[0][bb] = fma(xa, y, acc[0][bb]);
+                            acc[1][bb] = fma(xb, y, acc[1][bb]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // epilogue: dense workspace buffer, block of packed C, or upper part of a diagonal block
+        const Bind& bind = bs.b[sp.inst];
+        if (warp_rows) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int i = i0 + warp * 8 + 2 * lr + a;
+                if (i >= sp.out_rows) continue;
+#pragma unroll
+                for (int bb = 0; bb < 8; ++bb) {
+                    const int j = j0 + lc + 8 * bb;
+                    if (j >= sp.out_cols) continue;
+                    if (sp.out_kind == OUT_DENSE) {
+                        reinterpret_cast<double*>(bind.W)[sp.out_off + (int64_t)i * sp.out_ld + j] = acc[a][bb];
+                    } else {
+                        const int64_t gi = (int64_t)sp.ci0 + i, gj = (int64_t)sp.cj0 + j;
+                        if (sp.out_kind == OUT_SYRK && gj < gi) continue;
+                        bind.C[packed_start(gi, bind.n) + (gj - gi)] = acc[a][bb];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Operand split (Section 4.2.2 sums).  Each thread handles one (k, c) of the
+// K1 x c1 child block: it reads the four parent blocks once and writes every
+// sum of this side.  Output slot order matches the planner's table.
+template <int NB, typename TS, typename TD>
+__global__ void __launch_bounds__(256) split_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                    const SplitTask* __restrict__ tasks,
+                                                    const Chunk* __restrict__ chunks) {
+    const Chunk ch = chunks[blockIdx.x];
+    const SplitTask& st = tasks[ch.task];
+    const Bind& bind = bs.b[st.inst];
+    const int c1 = st.c1, K1 = st.K1;
+    const TS* src = term_ptr<TS>(bind, st.src);
+    const int64_t ld = st.src.ld;
+    const int srows = st.src.rows, scols = st.src.cols;
+    const bool neg = st.src.neg;
+    TD* W = reinterpret_cast<TD*>(bind.W);
+    const int total = ch.nrows * c1;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int k = ch.row0 + e / c1, c = e % c1;
+        TD B[4];
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+            for (int cb = 0; cb < 2; ++cb) {
+                const int rr = kb * K1 + k, cc = cb * c1 + c;
+                TD v = 0;
+                if (rr < srows && cc < scols) v = (TD)src[(int64_t)rr * ld + cc];
+                B[2 * kb + cb] = neg ? -v : v;
+            }
+        const int64_t o = (int64_t)k * c1 + c;
+        if (st.variant == 0) {
+            if (st.side == 0) {  // left factor X^t: M1 M2 M5 M6 M7
+                W[st.out_off[0] + o] = B[0] + B[3];
+                W[st.out_off[1] + o] = B[1] + B[3];
+                W[st.out_off[2] + o] = B[0] + B[2];
+                W[st.out_off[3] + o] = B[1] - B[0];
+                W[st.out_off[4] + o] = B[2] - B[3];
+            } else {             // right factor Y: M1 M3 M4 M6 M7
+                W[st.out_off[0] + o] = B[0] + B[3];
+                W[st.out_off[1] + o] = B[1] - B[3];
+                W[st.out_off[2] + o] = B[2] - B[0];
+                W[st.out_off[3] + o] = B[0] + B[1];
+                W[st.out_off[4] + o] = B[2] + B[3];
+            }
+        } else {
+            if (st.side == 0) {  // S1 S2 S3 S4 (Winograd, chained)
+                const TD s1 = B[1] + B[3];
+                const TD s2 = s1 - B[0];
+                W[st.out_off[0] + o] = s1;
+                W[st.out_off[1] + o] = s2;
+                W[st.out_off[2] + o] = B[0] - B[1];
+                W[st.out_off[3] + o] = B[2] - s2;
+            } else {             // T1 T2 T3 T4
+                const TD t1 = B[1] - B[0];
+                const TD t2 = B[3] - t1;
+                W[st.out_off[0] + o] = t1;
+                W[st.out_off[1] + o] = t2;
+                W[st.out_off[2] + o] = B[3] - B[1];
+                W[st.out_off[3] + o] = t2 - B[2];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Output combine (Section 4.2.2: D11..D22 from M1..M7, additions in the
+// printed order; Winograd's U-chain for the variant).  Each thread handles
+// one (i, j) of the p1 x r1 child grid and writes up to four quadrants.
+template <int NB>
+__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                      const CombineTask* __restrict__ tasks,
+                                                      const Chunk* __restrict__ chunks) {
+    const Chunk ch = chunks[blockIdx.x];
+    const CombineTask& ct = tasks[ch.task];
+    const Bind& bind = bs.b[ct.inst];
+    const int p = ct.p, r = ct.r, p1 = ct.p1, r1 = ct.r1;
+    const double* M = reinterpret_cast<const double*>(bind.W) + ct.m_off;
+    const int64_t msz = (int64_t)p1 * r1;
+    const int total = ch.nrows * r1;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int i = ch.row0 + e / r1, j = e % r1;
+        const int64_t o = (int64_t)i * r1 + j;
+        double m[7];
+#pragma unroll
+        for (int t = 0; t < 7; ++t) m[t] = M[t * msz + o];
+        double d[4];
+        if (ct.variant == 0) {
+            d[0] = m[0] - m[4] + m[6] + m[3];  // D11 = M1 - M5 + M7 + M4
+            d[1] = m[2] + m[4];                // D12 = M3 + M5
+            d[2] = m[1] + m[3];                // D21 = M2 + M4
+            d[3] = m[2] + m[5] - m[1] + m[0];  // D22 = M3 + M6 - M2 + M1
+        } else {
+            const double u2 = m[0] + m[5];     // U2 = M1 + M6
+            const double u3 = u2 + m[6];       // U3 = U2 + M7
+            d[0] = m[0] + m[1];                // D11 = M1 + M2
+            d[1] = (u2 + m[4]) + m[2];         // D12 = U4 + M3, U4 = U2 + M5
+            d[2] = u3 - m[3];                  // D21 = U3 - M4
+            d[3] = u3 + m[4];                  // D22 = U3 + M5
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ii = (q >> 1) * p1 + i, jj = (q & 1) * r1 + j;
+            if (ii >= p || jj >= r) continue;
+            if (ct.dst_kind == OUT_DENSE) {
+                reinterpret_cast<double*>(bind.W)[ct.dst_off + (int64_t)ii * ct.dst_ld + jj] = d[q];
+            } else {
+                const int64_t gi = (int64_t)ct.ci0 + ii, gj = (int64_t)ct.cj0 + jj;
+                bind.C[packed_start(gi, bind.n) + (gj - gi)] = d[q];
+            }
+        }
+    }
+}
+
+template <int NB>
+BindSet<NB> make_set(const Bind* binds, int nb) {
+    BindSet<NB> s{};
+    for (int i = 0; i < nb && i < NB; ++i) s.b[i] = binds[i];
+    return s;
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_f64(const Bind* binds, int nb, const LeafProduct* prods, const Term* terms,
+                            const LeafTile* tiles, int ntiles, int* counter, int grid, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (nb <= 1)
+        leaf_f64_kernel<1><<<grid, NTHREADS, 0, s>>>(make_set<1>(binds, nb), prods, terms, tiles, ntiles, counter);
+    else if (nb <= kMaxBatchBind)
+        leaf_f64_kernel<kMaxBatchBind><<<grid, NTHREADS, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), prods, terms,
+                                                                 tiles, ntiles, counter);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+int leaf_f64_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, leaf_f64_kernel<1>, NTHREADS, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+template <int NB>
+static cudaError_t split_dispatch(const BindSet<NB>& bs, const SplitTask* tasks, const Chunk* chunks, int nchunks,
+                                  int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
+    if (src_dt == DT_F64 && dst_dt == DT_F64)
+        split_kernel<NB, double, double><<<nchunks, 256, 0, s>>>(bs, tasks, chunks);
+    else if (src_dt == DT_F32 && dst_dt == DT_F32)
+        split_kernel<NB, float, float><<<nchunks, 256, 0, s>>>(bs, tasks, chunks);
+    else if (src_dt == DT_F32 && dst_dt == DT_F64)
+        split_kernel<NB, float, double><<<nchunks, 256, 0, s>>>(bs, tasks, chunks);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const Bind* binds, int nb, const SplitTask* tasks, const Chunk* chunks, int nchunks,
+                         int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    if (nb <= 1) return split_dispatch<1>(make_set<1>(binds, nb), tasks, chunks, nchunks, src_dt, dst_dt, s);
+    if (nb <= kMaxBatchBind)
+        return split_dispatch<kMaxBatchBind>(make_set<kMaxBatchBind>(binds, nb), tasks, chunks, nchunks, src_dt,
+                                             dst_dt, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_combine(const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks, int nchunks,
+                           cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    if (nb <= 1)
+        combine_kernel<1><<<nchunks, 256, 0, s>>>(make_set<1>(binds, nb), tasks, chunks);
+    else if (nb <= kMaxBatchBind)
+        combine_kernel<kMaxBatchBind><<<nchunks, 256, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), tasks, chunks);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace ata

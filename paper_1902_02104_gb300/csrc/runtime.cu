@@ -1,0 +1,627 @@
+// runtime.cu -- plans, device task tables, CUDA-graph execution and the C ABI
+// declared in include/ata.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ata.h"
+#include "kernels.h"
+#include "plan.h"
+#include "runtime.h"
+
+namespace ata {
+
+thread_local std::string g_last_error;
+
+ata_status fail(ata_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+ata_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return ATA_ECUDA;
+}
+
+#define ATA_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+static std::atomic<uint64_t> g_plan_ids{1};
+
+// ---------------------------------------------------------------------------
+// Host tables -> one device blob.
+
+static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+void build_chunks(int64_t rows, int64_t cols, int32_t task, std::vector<Chunk>* out) {
+    if (rows <= 0 || cols <= 0) return;
+    const int64_t per = std::max<int64_t>(1, (16384 + cols - 1) / cols);
+    for (int64_t r0 = 0; r0 < rows; r0 += per) {
+        Chunk c;
+        c.task = task;
+        c.row0 = (int32_t)r0;
+        c.nrows = (int32_t)std::min<int64_t>(per, rows - r0);
+        out->push_back(c);
+    }
+}
+
+ata_status upload_tables(const HostTables& h, DeviceTables* d) {
+    d->free_all();
+    int64_t off = 0;
+    auto place = [&](int64_t bytes) {
+        int64_t o = off;
+        off = align_up(off + std::max<int64_t>(bytes, 0), 256);
+        return o;
+    };
+    const int64_t o_terms = place(h.terms.size() * sizeof(Term));
+    const int64_t o_prods = place(h.prods.size() * sizeof(LeafProduct));
+    const int64_t o_tiles = place(h.tiles.size() * sizeof(LeafTile));
+    const int64_t o_cnt = place(64);
+    const int64_t o_split = place(h.split.size() * sizeof(SplitTask));
+    const int64_t o_schunk = place(h.split_chunks.size() * sizeof(Chunk));
+    const int64_t o_comb = place(h.comb.size() * sizeof(CombineTask));
+    const int64_t o_cchunk = place(h.comb_chunks.size() * sizeof(Chunk));
+    const int64_t total = std::max<int64_t>(off, 256);
+    char* blob = nullptr;
+    cudaError_t e = cudaMalloc(&blob, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ATA_ENOMEM, "task tables: cudaMalloc failed");
+    }
+    std::vector<char> hb(total, 0);
+    auto put = [&](int64_t o, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(hb.data() + o, src, bytes);
+    };
+    put(o_terms, h.terms.data(), h.terms.size() * sizeof(Term));
+    put(o_prods, h.prods.data(), h.prods.size() * sizeof(LeafProduct));
+    put(o_tiles, h.tiles.data(), h.tiles.size() * sizeof(LeafTile));
+    put(o_split, h.split.data(), h.split.size() * sizeof(SplitTask));
+    put(o_schunk, h.split_chunks.data(), h.split_chunks.size() * sizeof(Chunk));
+    put(o_comb, h.comb.data(), h.comb.size() * sizeof(CombineTask));
+    put(o_cchunk, h.comb_chunks.data(), h.comb_chunks.size() * sizeof(Chunk));
+    e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(blob);
+        return cuda_fail(e, "task tables: upload");
+    }
+    d->blob = blob;
+    d->terms = reinterpret_cast<Term*>(blob + o_terms);
+    d->prods = reinterpret_cast<LeafProduct*>(blob + o_prods);
+    d->tiles = reinterpret_cast<LeafTile*>(blob + o_tiles);
+    d->counter = reinterpret_cast<int*>(blob + o_cnt);
+    d->split = reinterpret_cast<SplitTask*>(blob + o_split);
+    d->split_chunks = reinterpret_cast<Chunk*>(blob + o_schunk);
+    d->comb = reinterpret_cast<CombineTask*>(blob + o_comb);
+    d->comb_chunks = reinterpret_cast<Chunk*>(blob + o_cchunk);
+    d->ntiles = (int)h.tiles.size();
+    d->split_lv = h.split_lv;
+    d->comb_lv = h.comb_lv;
+    d->leaf = h.leaf;
+    return ATA_OK;
+}
+
+// Appends plan `P` (instance `inst`, A leading dimension `lda`) to host tables.
+// Tables of several plans concatenate level by level (batched execution).
+void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h) {
+    const int32_t t_base = (int32_t)h->terms.size();
+    const int32_t p_base = (int32_t)h->prods.size();
+    auto fix_term = [&](Term t) {
+        t.inst = inst;
+        if (t.buf == BUF_A && P.n > 0) {
+            const int64_t row = t.off / P.n, col = t.off % P.n;
+            t.off = row * lda + col;
+            t.ld = lda;
+        }
+        return t;
+    };
+    for (const Term& t : P.terms) h->terms.push_back(fix_term(t));
+    for (LeafProduct lp : P.products) {
+        lp.x0 += t_base;
+        lp.y0 += t_base;
+        lp.inst = inst;
+        h->prods.push_back(lp);
+    }
+    for (size_t i = 0; i < P.products.size(); ++i) {
+        const LeafProduct& lp = P.products[i];
+        const int tm = kF64Tile;
+        const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tm - 1) / tm;
+        for (int64_t ti = 0; ti < a; ++ti)
+            for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti : 0); tj < b; ++tj) {
+                LeafTile t;
+                t.prod = p_base + (int32_t)i;
+                t.ti = (int32_t)ti;
+                t.tj = (int32_t)tj;
+                h->tiles.push_back(t);
+            }
+    }
+    // split / combine levels, merged level by level
+    if (h->split_lv.size() < P.split_levels.size()) h->split_lv.resize(P.split_levels.size());
+    if (h->comb_lv.size() < P.combine_levels.size()) h->comb_lv.resize(P.combine_levels.size());
+    for (size_t l = 0; l < P.split_levels.size(); ++l)
+        for (SplitTask st : P.split_levels[l]) {
+            st.src = fix_term(st.src);
+            st.inst = inst;
+            h->split_pending[l].push_back(st);
+        }
+    for (size_t l = 0; l < P.combine_levels.size(); ++l)
+        for (CombineTask ct : P.combine_levels[l]) {
+            ct.inst = inst;
+            h->comb_pending[l].push_back(ct);
+        }
+}
+
+// Orders leaf tiles heaviest first and lays out split/combine tasks and chunks
+// contiguously per level.
+void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt) {
+    std::stable_sort(h->tiles.begin(), h->tiles.end(), [&](const LeafTile& a, const LeafTile& b) {
+        return h->prods[a.prod].K > h->prods[b.prod].K;
+    });
+    for (size_t l = 0; l < h->split_lv.size(); ++l) {
+        LevelRange& lr = h->split_lv[l];
+        lr.chunk0 = (int32_t)h->split_chunks.size();
+        lr.src_dt = l == 0 ? in_dt : sum_dt;
+        lr.dst_dt = sum_dt;
+        for (const SplitTask& st : h->split_pending[l]) {
+            const int32_t tid = (int32_t)h->split.size();
+            h->split.push_back(st);
+            build_chunks(st.K1, st.c1, tid, &h->split_chunks);
+        }
+        lr.nchunks = (int32_t)h->split_chunks.size() - lr.chunk0;
+    }
+    for (size_t l = 0; l < h->comb_lv.size(); ++l) {
+        LevelRange& lr = h->comb_lv[l];
+        lr.chunk0 = (int32_t)h->comb_chunks.size();
+        for (const CombineTask& ct : h->comb_pending[l]) {
+            const int32_t tid = (int32_t)h->comb.size();
+            h->comb.push_back(ct);
+            build_chunks(ct.p1, ct.r1, tid, &h->comb_chunks);
+        }
+        lr.nchunks = (int32_t)h->comb_chunks.size() - lr.chunk0;
+    }
+    h->split_pending.clear();
+    h->comb_pending.clear();
+}
+
+void DeviceTables::free_all() {
+    if (blob) cudaFree(blob);
+    blob = nullptr;
+}
+
+// Queues one execution of `t` with bindings `binds` on `s` (no graph).
+// SM count and resident leaf blocks per SM of the current device (queried
+// outside any stream capture, once per process).
+static void device_params(int* sms, int* per_sm) {
+    static int s_sms = -1, s_per = -1;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (s_sms < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&s_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s_sms <= 0)
+            s_sms = 1;
+        s_per = leaf_f64_blocks_per_sm();
+    }
+    *sms = s_sms;
+    *per_sm = s_per;
+}
+
+ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s, const cudaEvent_t* ev) {
+    int sms = 1, per_sm = 1;
+    device_params(&sms, &per_sm);
+    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
+    for (size_t l = 0; l < t.split_lv.size(); ++l) {
+        const LevelRange& lr = t.split_lv[l];
+        ATA_CUDA(launch_split(binds, nb, t.split, t.split_chunks + lr.chunk0, lr.nchunks, lr.src_dt, lr.dst_dt, s));
+    }
+    if (t.ntiles > 0) ATA_CUDA(cudaMemsetAsync(t.counter, 0, sizeof(int), s));
+    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
+    if (t.ntiles > 0) {
+        if (t.leaf == LEAF_F64) {
+            const int grid = std::max(1, std::min(t.ntiles, sms * per_sm));
+            ATA_CUDA(launch_leaf_f64(binds, nb, t.prods, t.terms, t.tiles, t.ntiles, t.counter, grid, s));
+        } else {
+            ata_status st = launch_leaf_tc(t, binds, nb, s);
+            if (st != ATA_OK) return st;
+        }
+    }
+    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
+    for (int l = (int)t.comb_lv.size() - 1; l >= 0; --l) {
+        const LevelRange& lr = t.comb_lv[l];
+        ATA_CUDA(launch_combine(binds, nb, t.comb, t.comb_chunks + lr.chunk0, lr.nchunks, s));
+    }
+    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
+    return ATA_OK;
+}
+
+// Captures the launches of `t` into a graph and instantiates (or updates) `g`.
+ata_status capture_graph(const DeviceTables& t, const Bind* binds, int nb, GraphCache* g) {
+    if (!g->cap_stream) ATA_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    if (g->timing && !g->ev[0])
+        for (int i = 0; i < 4; ++i) ATA_CUDA(cudaEventCreate(&g->ev[i]));
+    {
+        int sms, per_sm;
+        device_params(&sms, &per_sm);  // before capture: attribute queries are not captured work
+    }
+    ATA_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ata_status st = enqueue_tables(t, binds, nb, g->cap_stream, g->timing ? g->ev : nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (st != ATA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if (g->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g->exec, graph, &info) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return ATA_OK;
+        }
+        cudaGetLastError();
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return ATA_OK;
+}
+
+void GraphCache::release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (int i = 0; i < 4; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 4; ++i) ev[i] = nullptr;
+    exec = nullptr;
+    cap_stream = nullptr;
+    binds.clear();
+    timed_run = false;
+}
+
+bool same_binds(const std::vector<Bind>& a, const Bind* b, int nb) {
+    if ((int)a.size() != nb) return false;
+    for (int i = 0; i < nb; ++i)
+        if (a[i].A != b[i].A || a[i].C != b[i].C || a[i].W != b[i].W || a[i].n != b[i].n) return false;
+    return true;
+}
+
+// Launches the tables through the cached graph (captured on first use or
+// when the bindings change).
+ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, GraphCache* g, cudaStream_t s) {
+    if (!g->exec || !same_binds(g->binds, binds, nb)) {
+        ata_status st = capture_graph(t, binds, nb, g);
+        if (st != ATA_OK) return st;
+        g->binds.assign(binds, binds + nb);
+    }
+    ATA_CUDA(cudaGraphLaunch(g->exec, s));
+    g->timed_run = g->timing;
+    return ATA_OK;
+}
+
+}  // namespace ata
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace ata;
+
+struct ata_plan_s {
+    uint64_t id = 0;
+    Plan plan;
+    ata_dtype dtype = ATA_F64;
+    int device = 0;
+    char* ws = nullptr;
+    int64_t lda = -1;           // leading dimension the device tables are built for
+    DeviceTables tables;
+    GraphCache graph;
+    std::mutex mu;
+    // staging for ata_execute_host
+    void* stage_A = nullptr;
+    double* stage_C = nullptr;
+    ~ata_plan_s() {
+        graph.release();
+        tables.free_all();
+        if (ws) cudaFree(ws);
+        if (stage_A) cudaFree(stage_A);
+        if (stage_C) cudaFree(stage_C);
+    }
+};
+
+namespace {
+
+int elem_bytes(ata_dtype d) { return (d == ATA_F64 || d == ATA_F64_OZAKI) ? 8 : 4; }
+
+bool valid_dtype(int d) { return d >= ATA_F64 && d <= ATA_F64_OZAKI; }
+
+LeafKind leaf_of(ata_dtype d) {
+    switch (d) {
+        case ATA_F32_BF16X3: return LEAF_BF16X3;
+        case ATA_F32_TF32: return LEAF_TF32;
+        case ATA_F64_OZAKI: return LEAF_OZAKI;
+        default: return LEAF_F64;
+    }
+}
+
+ata_status make_options(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options& u, PlanOptions* o) {
+    if (m < 0 || n < 0) return fail(ATA_EINVAL, "m and n must be >= 0");
+    if (!valid_dtype(dtype)) return fail(ATA_EINVAL, "unknown dtype");
+    const int cutoff = u.cutoff;
+    if (cutoff != 0 && (cutoff < 16 || cutoff > 4096)) return fail(ATA_EINVAL, "cutoff must be 0 or in [16, 4096]");
+    const int variant = u.variant < 0 ? ATA_STRASSEN : u.variant;
+    if (variant != ATA_STRASSEN && variant != ATA_WINOGRAD) return fail(ATA_EINVAL, "unknown variant");
+    if (u.fuse_levels < -1 || u.fuse_levels > 16) return fail(ATA_EINVAL, "fuse_levels must be -1 or in [0, 16]");
+    if (u.max_strassen_levels < -1 || u.max_strassen_levels > 64)
+        return fail(ATA_EINVAL, "max_strassen_levels must be -1 or in [0, 64]");
+    o->leaf = leaf_of(dtype);
+    o->variant = variant;
+    o->cutoff = cutoff != 0 ? cutoff : default_cutoff(m, n, dtype);
+    o->fuse_levels = u.fuse_levels >= 0 ? u.fuse_levels : default_fuse_levels(dtype, variant);
+    o->max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : 64;
+    return ATA_OK;
+}
+
+ata_plan_options default_opts(int cutoff, int variant) {
+    ata_plan_options u;
+    u.cutoff = cutoff;
+    u.variant = variant;
+    u.fuse_levels = -1;
+    u.max_strassen_levels = -1;
+    return u;
+}
+
+void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
+    std::memset(out, 0, sizeof(*out));
+    out->m = P.m;
+    out->n = P.n;
+    out->dtype = dtype;
+    out->cutoff = P.cutoff;
+    out->depth = P.stats.depth;
+    out->n_diag_leaves = P.stats.n_diag_leaves;
+    out->n_nodes = P.stats.n_nodes;
+    out->max_strassen_levels = P.stats.max_strassen_levels;
+    out->n_leaf_products = (int32_t)P.products.size();
+    int64_t tiles = 0;
+    for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, kF64Tile, kF64Tile);
+    out->n_leaf_tiles = (int32_t)tiles;
+    int64_t ns = 0, nc = 0;
+    for (auto& v : P.split_levels) ns += v.size();
+    for (auto& v : P.combine_levels) nc += v.size();
+    out->n_sum_tasks = (int32_t)ns;
+    out->n_combine_tasks = (int32_t)nc;
+    out->n_launches = (int32_t)(P.split_levels.size() + P.combine_levels.size() + (P.products.empty() ? 0 : 1));
+    out->mults = P.stats.mults;
+    out->classical_mults = P.m * P.n * (P.n + 1) / 2;
+    out->adds = P.stats.adds;
+    out->workspace_bytes = P.ws_bytes;
+}
+
+ata_status check_terms(const Plan& P) {
+    for (const LeafProduct& lp : P.products)
+        if (lp.nx > kMaxTerms || lp.ny > kMaxTerms)
+            return fail(ATA_EUNSUPPORTED, "a leaf operand has more fused terms than the kernels accept");
+    return ATA_OK;
+}
+
+ata_status rebuild_tables(ata_plan plan, int64_t lda) {
+    HostTables h;
+    h.leaf = plan->plan.leaf;
+    h.split_pending.resize(plan->plan.split_levels.size());
+    h.comb_pending.resize(plan->plan.combine_levels.size());
+    append_plan_tables(plan->plan, 0, lda, &h);
+    finalize_tables(&h, plan->plan.in_dt, plan->plan.sum_dt);
+    ata_status st = upload_tables(h, &plan->tables);
+    if (st != ATA_OK) return st;
+    plan->lda = lda;
+    plan->graph.release();
+    return ATA_OK;
+}
+
+ata_status check_ptr(const void* p, int align, const char* what) {
+    if (reinterpret_cast<uintptr_t>(p) % align != 0)
+        return fail(ATA_EINVAL, std::string(what) + " is not aligned to its element size");
+    return ATA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ata_status_string(ata_status s) {
+    switch (s) {
+        case ATA_OK: return "ATA_OK";
+        case ATA_EINVAL: return "ATA_EINVAL";
+        case ATA_ENOMEM: return "ATA_ENOMEM";
+        case ATA_EUNSUPPORTED: return "ATA_EUNSUPPORTED";
+        case ATA_ECUDA: return "ATA_ECUDA";
+        case ATA_PENDING: return "ATA_PENDING";
+        case ATA_ETIMEOUT: return "ATA_ETIMEOUT";
+        case ATA_EBUSY: return "ATA_EBUSY";
+    }
+    return "ATA_UNKNOWN";
+}
+
+const char* ata_last_error_message(void) { return g_last_error.c_str(); }
+
+ata_status ata_plan_query(int64_t m, int64_t n, ata_dtype dtype, int cutoff, ata_plan_info* out) {
+    const ata_plan_options u = default_opts(cutoff, ATA_STRASSEN);
+    return ata_plan_query_opts(m, n, dtype, &u, out);
+}
+
+ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts,
+                               ata_plan_info* out) {
+    if (!out || !opts) return fail(ATA_EINVAL, "NULL argument");
+    PlanOptions o;
+    ata_status st = make_options(m, n, dtype, *opts, &o);
+    if (st != ATA_OK) return st;
+    if (opts->cutoff == 0) {
+        st = autotune_cutoff(m, n, dtype, o.variant, &o);
+        if (st != ATA_OK) return st;
+    }
+    Plan P;
+    std::string err;
+    if (!build_plan(m, n, o, &P, &err)) return fail(ATA_EINVAL, err);
+    fill_info(P, dtype, out);
+    return ATA_OK;
+}
+
+ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
+    if (!out || !opts) return fail(ATA_EINVAL, "NULL argument");
+    *out = nullptr;
+    PlanOptions o;
+    ata_status st = make_options(m, n, dtype, *opts, &o);
+    if (st != ATA_OK) return st;
+    if (opts->cutoff == 0) {
+        st = autotune_cutoff(m, n, dtype, o.variant, &o);
+        if (st != ATA_OK) return st;
+    }
+    std::unique_ptr<ata_plan_s> p(new ata_plan_s());
+    std::string err;
+    if (!build_plan(m, n, o, &p->plan, &err)) return fail(ATA_EINVAL, err);
+    st = check_terms(p->plan);
+    if (st != ATA_OK) return st;
+    if (!leaf_supported(p->plan.leaf)) return fail(ATA_EUNSUPPORTED, "leaf kind not built into this library");
+    p->id = g_plan_ids.fetch_add(1);
+    p->dtype = dtype;
+    ATA_CUDA(cudaGetDevice(&p->device));
+    if (p->plan.ws_bytes > 0) {
+        cudaError_t e = cudaMalloc(&p->ws, p->plan.ws_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->ws = nullptr;
+            return fail(ATA_ENOMEM, "workspace: cudaMalloc of " + std::to_string(p->plan.ws_bytes) + " bytes failed");
+        }
+    }
+    st = rebuild_tables(p.get(), n);
+    if (st != ATA_OK) return st;
+    *out = p.release();
+    return ATA_OK;
+}
+
+ata_status ata_plan_create(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype, int cutoff) {
+    const ata_plan_options u = default_opts(cutoff, ATA_STRASSEN);
+    return ata_plan_create_opts(out, m, n, dtype, &u);
+}
+
+ata_status ata_plan_get_info(ata_plan plan, ata_plan_info* out) {
+    if (!plan || !out) return fail(ATA_EINVAL, "NULL argument");
+    fill_info(plan->plan, plan->dtype, out);
+    return ATA_OK;
+}
+
+ata_status ata_plan_workspace_size(ata_plan plan, size_t* bytes) {
+    if (!plan || !bytes) return fail(ATA_EINVAL, "NULL argument");
+    *bytes = (size_t)plan->plan.ws_bytes;
+    return ATA_OK;
+}
+
+ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_packed, void* stream) {
+    if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    const int64_t m = plan->plan.m, n = plan->plan.n;
+    if (lda < n || lda < 1) return fail(ATA_EINVAL, "lda must be >= max(n, 1)");
+    if (m > 0 && n > 0 && !A) return fail(ATA_EINVAL, "A is NULL");
+    if (n > 0 && !C_packed) return fail(ATA_EINVAL, "C_packed is NULL");
+    ata_status st = check_ptr(A, elem_bytes(plan->dtype), "A");
+    if (st != ATA_OK) return st;
+    st = check_ptr(C_packed, 8, "C_packed");
+    if (st != ATA_OK) return st;
+    if (n == 0) return ATA_OK;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (lda != plan->lda) {
+        // the stream may still run the previous tables
+        ATA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        st = rebuild_tables(plan, lda);
+        if (st != ATA_OK) return st;
+    }
+    Bind b{A, C_packed, plan->ws, n};
+    return launch_via_graph(plan->tables, &b, 1, &plan->graph, static_cast<cudaStream_t>(stream));
+}
+
+ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, double* C_host, void* stream) {
+    if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    const int64_t m = plan->plan.m, n = plan->plan.n;
+    const int es = elem_bytes(plan->dtype);
+    if (lda < n || lda < 1) return fail(ATA_EINVAL, "lda must be >= max(n, 1)");
+    if (m > 0 && n > 0 && !A_host) return fail(ATA_EINVAL, "A is NULL");
+    if (n > 0 && !C_host) return fail(ATA_EINVAL, "C_packed is NULL");
+    if (n == 0) return ATA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lk(plan->mu);
+        if (!plan->stage_A && m > 0) {
+            if (cudaMalloc(&plan->stage_A, (size_t)m * n * es) != cudaSuccess) {
+                cudaGetLastError();
+                plan->stage_A = nullptr;
+                return fail(ATA_ENOMEM, "staging buffer for A");
+            }
+        }
+        if (!plan->stage_C) {
+            if (cudaMalloc(&plan->stage_C, (size_t)(n * (n + 1) / 2) * 8) != cudaSuccess) {
+                cudaGetLastError();
+                plan->stage_C = nullptr;
+                return fail(ATA_ENOMEM, "staging buffer for C");
+            }
+        }
+    }
+    if (m > 0)
+        ATA_CUDA(cudaMemcpy2DAsync(plan->stage_A, (size_t)n * es, A_host, (size_t)lda * es, (size_t)n * es, (size_t)m,
+                                   cudaMemcpyHostToDevice, s));
+    ata_status st = ata_execute(plan, plan->stage_A ? plan->stage_A : (const void*)plan->stage_C, n, plan->stage_C, stream);
+    if (st != ATA_OK) return st;
+    ATA_CUDA(cudaMemcpyAsync(C_host, plan->stage_C, (size_t)(n * (n + 1) / 2) * 8, cudaMemcpyDeviceToHost, s));
+    ATA_CUDA(cudaStreamSynchronize(s));
+    return ATA_OK;
+}
+
+ata_status ata_plan_enable_stage_timing(ata_plan plan, int enable) {
+    if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    std::lock_guard<std::mutex> lk(plan->mu);
+    const bool want = enable != 0;
+    if (want != plan->graph.timing) {
+        plan->graph.release();
+        plan->graph.timing = want;
+    }
+    return ATA_OK;
+}
+
+ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms, float* combine_ms) {
+    if (!plan || !split_ms || !leaf_ms || !combine_ms) return fail(ATA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (!plan->graph.timing || !plan->graph.timed_run || !plan->graph.ev[0])
+        return fail(ATA_EINVAL, "stage timing is not enabled or nothing has run");
+    ATA_CUDA(cudaEventElapsedTime(split_ms, plan->graph.ev[0], plan->graph.ev[1]));
+    ATA_CUDA(cudaEventElapsedTime(leaf_ms, plan->graph.ev[1], plan->graph.ev[2]));
+    ATA_CUDA(cudaEventElapsedTime(combine_ms, plan->graph.ev[2], plan->graph.ev[3]));
+    return ATA_OK;
+}
+
+void ata_plan_destroy(ata_plan plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    forget_plan_in_batches(plan->id);
+    delete plan;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Accessors used by the batched and serving layers.
+namespace ata {
+const Plan& plan_of(ata_plan p) { return p->plan; }
+uint64_t plan_id(ata_plan p) { return p->id; }
+char* plan_workspace(ata_plan p) { return p->ws; }
+ata_dtype plan_dtype(ata_plan p) { return p->dtype; }
+}  // namespace ata

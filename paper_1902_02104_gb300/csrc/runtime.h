@@ -1,0 +1,94 @@
+// runtime.h -- internal runtime types shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ata.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace ata {
+
+// Chunks of one split or combine level.
+struct LevelRange {
+    int32_t chunk0 = 0, nchunks = 0;
+    int8_t src_dt = DT_F64, dst_dt = DT_F64;
+};
+
+// Task tables on the host, ready to upload (one plan or a merged batch).
+struct HostTables {
+    LeafKind leaf = LEAF_F64;
+    std::vector<Term> terms;
+    std::vector<LeafProduct> prods;
+    std::vector<LeafTile> tiles;
+    std::vector<SplitTask> split;
+    std::vector<Chunk> split_chunks;
+    std::vector<LevelRange> split_lv;
+    std::vector<CombineTask> comb;
+    std::vector<Chunk> comb_chunks;
+    std::vector<LevelRange> comb_lv;
+    std::vector<std::vector<SplitTask>> split_pending;
+    std::vector<std::vector<CombineTask>> comb_pending;
+};
+
+// The same tables in device memory (one allocation).
+struct DeviceTables {
+    LeafKind leaf = LEAF_F64;
+    char* blob = nullptr;
+    Term* terms = nullptr;
+    LeafProduct* prods = nullptr;
+    LeafTile* tiles = nullptr;
+    int ntiles = 0;
+    int* counter = nullptr;
+    SplitTask* split = nullptr;
+    Chunk* split_chunks = nullptr;
+    std::vector<LevelRange> split_lv;
+    CombineTask* comb = nullptr;
+    Chunk* comb_chunks = nullptr;
+    std::vector<LevelRange> comb_lv;
+    void free_all();
+};
+
+// An instantiated CUDA graph of one table set and the bindings it was
+// captured with.
+struct GraphCache {
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Bind> binds;
+    bool timing = false;        // graph records ev[] around its stages
+    bool timed_run = false;     // an execution with timing has been queued
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void release();
+};
+
+extern thread_local std::string g_last_error;
+ata_status fail(ata_status s, const std::string& msg);
+ata_status cuda_fail(cudaError_t e, const char* what);
+
+void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h);
+void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt);
+ata_status upload_tables(const HostTables& h, DeviceTables* d);
+ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s,
+                          const cudaEvent_t* ev = nullptr);
+ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, GraphCache* g, cudaStream_t s);
+
+// Tensor-core leaf launch (bf16x3 / TF32 / FP64 emulation).
+ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s);
+bool leaf_supported(LeafKind k);
+
+// Planner defaults and the autotuner.
+int default_cutoff(int64_t m, int64_t n, ata_dtype dtype);
+int default_fuse_levels(ata_dtype dtype, int variant);
+ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o);
+
+// Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
+const Plan& plan_of(ata_plan p);
+uint64_t plan_id(ata_plan p);
+char* plan_workspace(ata_plan p);
+ata_dtype plan_dtype(ata_plan p);
+void forget_plan_in_batches(uint64_t id);
+
+}  // namespace ata

@@ -1,0 +1,43 @@
+"""The C-ABI library loads and exports every function include/ata.h declares
+(no GPU work here)."""
+import ctypes
+import os
+import re
+
+import paper_1902_02104_gb300 as ata
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ata_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ctypes.CDLL(ata.load()._name)
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings():
+    lib = ata.load()
+    assert lib.ata_status_string(0) == b"ATA_OK"
+    assert lib.ata_status_string(7) == b"ATA_EBUSY"
+
+
+def test_null_plan_rejected_without_device_work():
+    lib = ata.load()
+    assert lib.ata_execute(None, None, 1, None, None) == ata.ATA_EINVAL
+    assert lib.ata_plan_workspace_size(None, None) == ata.ATA_EINVAL
+    assert lib.ata_execute_batched(None, -1, None, None, None, None) == ata.ATA_EINVAL
+    assert lib.ata_execute_batched(None, 0, None, None, None, None) == ata.ATA_OK
+    assert b"NULL" in lib.ata_last_error_message() or lib.ata_last_error_message() != b""

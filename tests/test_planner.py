@@ -1,0 +1,87 @@
+"""Host-side planner checks (no GPU): tree shapes, multiplication counts,
+workspace, argument validation -- through the C ABI's ata_plan_query."""
+import numpy as np
+import pytest
+
+import paper_1902_02104_gb300 as ata
+from oracle import ata_recursive as R
+from tests.test_oracle import paper_recurrence
+
+
+def q(m, n, cutoff, dtype=ata.ATA_F64, **kw):
+    return ata.ata_plan_query(m, n, dtype, cutoff, **kw)
+
+
+def test_config1_tree():
+    # 512 x 384, cutoff 64: 512x384 -> 256x192 -> 128x96 -> 64x48 (Eq. "submatrices")
+    i = q(512, 384, 64)
+    assert i["depth"] == 3
+    assert i["n_diag_leaves"] == 8
+    assert i["n_nodes"] == 7
+    assert i["max_strassen_levels"] == 2
+    assert i["classical_mults"] == 512 * 384 * 385 // 2
+
+
+@pytest.mark.parametrize("N,c", [(128, 16), (256, 32), (512, 64), (1024, 64), (2048, 256)])
+def test_counts_match_paper_recurrence(N, c):
+    assert q(N, N, c)["mults"] == paper_recurrence(N, c)
+
+
+@pytest.mark.parametrize("m,n,c", [(512, 384, 64), (256, 256, 32), (100, 300, 32), (1024, 1024, 64)])
+def test_counts_match_algorithm1_restatement(m, n, c):
+    cnt = R.MultCounter()
+    R.ata(np.zeros((m, n)), c, cnt)
+    assert q(m, n, c)["mults"] == cnt.mults
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (17, 5), (513, 385), (1000, 3000), (3000, 1000)])
+def test_classical_when_strassen_disabled(m, n):
+    i = q(m, n, 16, max_strassen_levels=0)
+    assert i["mults"] == m * n * (n + 1) // 2
+    assert i["workspace_bytes"] == 0
+    assert i["n_leaf_products"] == i["n_diag_leaves"] + i["n_nodes"]
+
+
+def test_strassen_saves_multiplications():
+    for m, n, c in [(10000, 10000, 256), (20000, 8000, 256), (5000, 5000, 256)]:
+        i = q(m, n, c)
+        assert i["mults"] < 0.7 * i["classical_mults"]
+
+
+def test_leaf_counts_and_fusion():
+    a = q(1024, 1024, 64, fuse_levels=0)
+    b = q(1024, 1024, 64, fuse_levels=1)
+    assert a["mults"] == b["mults"]
+    assert a["n_leaf_products"] == b["n_leaf_products"]
+    assert a["n_sum_tasks"] > b["n_sum_tasks"]
+    assert a["workspace_bytes"] > b["workspace_bytes"]
+
+
+def test_degenerate_shapes():
+    i = q(0, 10, 64)
+    assert i["n_diag_leaves"] == 1 and i["mults"] == 0
+    i = q(10, 0, 64)
+    assert i["n_leaf_products"] == 0
+    i = q(1000, 1, 64)
+    assert i["n_diag_leaves"] == 1 and i["mults"] == 1000
+
+
+@pytest.mark.parametrize("bad", [dict(m=-1, n=3, cutoff=64), dict(m=3, n=-1, cutoff=64),
+                                 dict(m=3, n=3, cutoff=15), dict(m=3, n=3, cutoff=5000)])
+def test_invalid_arguments(bad):
+    with pytest.raises(ata.AtaError) as e:
+        q(bad["m"], bad["n"], bad["cutoff"])
+    assert e.value.status == ata.ATA_EINVAL
+
+
+def test_invalid_dtype_and_variant():
+    with pytest.raises(ata.AtaError):
+        ata.ata_plan_query(10, 10, 9, 64)
+    with pytest.raises(ata.AtaError):
+        ata.ata_plan_query(10, 10, 0, 64, variant=5)
+
+
+def test_autotune_picks_a_listed_cutoff():
+    i = q(10000, 10000, 0)
+    assert 64 <= i["cutoff"] <= 2048
+    assert i["workspace_bytes"] <= 48 << 30

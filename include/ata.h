@@ -199,6 +199,29 @@ ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms,
 /* Release the plan (waits for its queued work first). */
 void ata_plan_destroy(ata_plan plan);
 
+/* C_packed = A^t A (FP64, as ata_execute with ATA_F64 and the given
+ * cutoff) without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * while they run -- code that is about to capture a CUDA graph, services
+ * that fix their device-memory footprint at start-up, and hosts whose device
+ * memory belongs to another allocator.  The task tables, the tile counter
+ * and the Strassen workspace live in a static device array of 64 MiB built
+ * into the library (every GPU that loads the library holds it until the
+ * process exits); the caller passes A and C_packed (device pointers,
+ * layouts as above).
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call
+ * shares the one array and overwrites what the previous call left there, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race; calls queued on one stream are ordered.  The host task tables are
+ * copied into the array with cudaMemcpyAsync on `stream`.
+ * Errors: ATA_EINVAL (bad sizes or pointers, cutoff outside [16, 4096], or a
+ * problem whose tables and workspace exceed the 64 MiB array -- use
+ * ata_execute or a larger cutoff), ATA_ECUDA. */
+ata_status ata_execute_static_scratch(int64_t m, int64_t n, const double* A,
+                                      int64_t lda, double* C_packed,
+                                      int cutoff, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Serving: continuous batching of independent requests.               */
 /* ------------------------------------------------------------------ */

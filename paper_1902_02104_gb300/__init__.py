@@ -85,6 +85,7 @@ def load():
         "ata_execute_batched": ([ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                  ctypes.POINTER(vp), vp], i32),
         "ata_plan_destroy": ([vp], None),
+        "ata_execute_static_scratch": ([i64, i64, vp, i64, dp, i32, vp], i32),
         "ata_plan_enable_stage_timing": ([vp, i32], i32),
         "ata_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_float)], i32),
@@ -249,6 +250,24 @@ def ata_execute_batched(plans, As, Cs=None, stream=None):
     cp = (ctypes.c_void_p * count)(*[C.data_ptr() for C in Cs])
     _check(load().ata_execute_batched(ph, count, ap, ld, cp, _stream_handle(stream)))
     return Cs
+
+
+def ata_execute_static_scratch(A, C=None, cutoff: int = 64, stream=None):
+    """FP64 C_packed = A^t A with no device allocation: scratch comes from a
+    64 MiB array inside the library, shared by every call (calls that overlap
+    on the GPU race).  A is an m x n float64 CUDA tensor, row-major."""
+    import torch
+    if not A.is_cuda or A.dtype != torch.float64 or A.dim() != 2:
+        raise ValueError("A must be a 2-D float64 CUDA tensor")
+    m, n = A.shape
+    if m > 0 and n > 0 and A.stride(1) != 1:
+        raise ValueError("A must be row-major (unit column stride)")
+    lda = max(A.stride(0), n, 1) if m > 1 else max(n, 1)
+    if C is None:
+        C = torch.empty(packed_size(n), dtype=torch.float64, device=A.device)
+    _check(load().ata_execute_static_scratch(m, n, ctypes.c_void_p(A.data_ptr()), lda,
+                                             ctypes.c_void_p(C.data_ptr()), int(cutoff), _stream_handle(stream)))
+    return C
 
 
 class Server:

@@ -40,6 +40,8 @@ WORKLOADS = {
     "ata_f64_5000x5000": (5000, 5000, "f64", "normal", 1, 0),
     "ata_f64_20000x8000": (20000, 8000, "f64", "normal", 1, 0),
     "ata_f64_512x384": (512, 384, "f64", "uniform", 0, 64),
+    # small case for ncu captures of the leaf kernel (A 162 MB > L2, ~1 GB workspace)
+    "ata_f64_4500x4500_c600": (4500, 4500, "f64", "normal", 1, 600),
 }
 DEFAULT_WORKLOAD = "ata_f64_10000x10000"
 

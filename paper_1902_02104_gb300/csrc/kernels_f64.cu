@@ -5,10 +5,10 @@
 // 1.20 TFLOP/s on 152 SMs; DMMA is slower, 1.05 TFLOP/s), so the FP64 leaf
 // is a SIMT DFMA kernel and is bound by that pipe: a 64 x 64 tile with a K
 // slab of 16 takes ~32k clocks of DFMA per block while its 16 KB of operand
-// loads take a few hundred, so no load pipelining is needed.  What matters is
-// not issuing DFMAs on padding: work is skipped at 8 x 8 granularity (warp-
-// uniform branches) outside the valid extent and below the diagonal of
-// symmetric (SYRK) tiles.
+// loads take a few hundred.  What matters is that the pipe runs only useful
+// DFMAs: no FP64 additions in the operand loads, and no DFMA issued on
+// padding (work is skipped in 16 x 32 warp blocks outside the valid extent
+// and below the diagonal of symmetric (SYRK) tiles).
 #include <cstdint>
 
 #include "kernels.h"
@@ -26,9 +26,17 @@ __device__ __forceinline__ const T* term_ptr(const Bind& b, const Term& t) {
 }
 
 // Value of a fused operand (sum of signed terms) at (k, c); zero outside
-// each term's valid extent (implicit zero padding of uneven blocks).
+// each term's valid extent (implicit zero padding of uneven blocks).  A
+// single term (every materialised operand) needs no FP64 addition: its sign
+// is applied to the bit pattern, so the FP64 pipe only runs the leaf DFMAs.
 template <int NB>
 __device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* ts, int nt, int k, int c) {
+    if (nt == 1) {
+        const Term& tm = ts[0];
+        if (k >= tm.rows || c >= tm.cols) return 0.0;
+        const double x = __ldg(term_ptr<double>(bs.b[tm.inst], tm) + (int64_t)k * tm.ld + c);
+        return __longlong_as_double(__double_as_longlong(x) ^ ((long long)tm.neg << 63));
+    }
     double v = 0.0;
     for (int t = 0; t < nt; ++t) {
         const Term& tm = ts[t];
@@ -43,19 +51,27 @@ __device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* 
 constexpr int TILE = kF64Tile;  // 64
 constexpr int BK = 16;
 constexpr int NTHREADS = 256;
+constexpr int LOADS = (BK * TILE) / NTHREADS;  // operand elements per thread per slab and side
 
 // Persistent leaf kernel: blocks pull tiles (heaviest first) from a counter.
-// out(p x r) = X^t Y where X (K x p) and Y (K x r) are term sums.  Each warp
-// owns 8 tile rows; lane (lr, lc) owns rows 2lr, 2lr+1 of that strip and
-// columns lc + 8b, b = 0..7.  Accumulation runs k ascending per entry.
+// out(p x r) = X^t Y where X (K x p) and Y (K x r) are term sums.
+//
+// Warp w owns the 16 x 32 block (rows 16*(w/2).., cols 32*(w%2)..) of the
+// 64 x 64 tile; lane (lr, lc) owns rows 4lr..4lr+3 of it and columns
+// lc + 8b, b = 0..3.  Raggedness is therefore warp-uniform: a warp whose
+// block lies outside the valid extent (or strictly below the diagonal of a
+// symmetric tile) skips the whole slab with a branch, and active warps run
+// unpredicated DFMAs -- a predicated-off DFMA still occupies the FP64 pipe.
+// K is staged in slabs of 16, double-buffered through registers.
+// Accumulation runs k ascending per entry.
 template <int NB>
 __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constant__ BindSet<NB> bs,
                                                             const LeafProduct* __restrict__ prods,
                                                             const Term* __restrict__ terms,
                                                             const LeafTile* __restrict__ tiles, int ntiles,
                                                             int* __restrict__ counter) {
-    __shared__ double Xs[BK][TILE];
-    __shared__ double Ys[BK][TILE];
+    __shared__ __align__(16) double Xs[2][BK][TILE];
+    __shared__ __align__(16) double Ys[2][BK][TILE];
     __shared__ Term sx[kMaxTerms], sy[kMaxTerms];
     __shared__ int s_tile;
     __shared__ LeafProduct sp;
@@ -63,6 +79,8 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int lr = lane >> 3, lc = lane & 7;
+    const int row0 = 16 * (warp >> 1) + 4 * lr;  // first of this lane's 4 rows
+    const int col0 = 32 * (warp & 1) + lc;       // first of this lane's 4 columns (stride 8)
 
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(counter, 1);
@@ -82,64 +100,84 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
         const int K = sp.K;
         __syncthreads();
 
-        const bool warp_rows = warp * 8 < rows_v;
-        bool bval[8];
-#pragma unroll
-        for (int bb = 0; bb < 8; ++bb)
-            bval[bb] = warp_rows && (8 * bb < cols_v) && (!diag || 8 * bb + 7 >= warp * 8);
+        // warp-uniform activity: some valid row, some valid column, and not
+        // entirely below the diagonal of a symmetric tile
+        const int wr = 16 * (warp >> 1), wc = 32 * (warp & 1);
+        const bool active = wr < rows_v && wc < cols_v && (!diag || wc + 31 >= wr);
 
-        double acc[2][8];
+        double acc[4][4];
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int bb = 0; bb < 8; ++bb) acc[a][bb] = 0.0;
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-        for (int k0 = 0; k0 < K; k0 += BK) {
-            // stage the fused operand slabs (BK x 64 each); columns are contiguous in memory
+        double px[LOADS], py[LOADS];
+        auto fetch = [&](int k0) {
 #pragma unroll
-            for (int e = 0; e < (BK * TILE) / NTHREADS; ++e) {
+            for (int e = 0; e < LOADS; ++e) {
                 const int idx = tid + e * NTHREADS;
                 const int kk = idx / TILE, c = idx % TILE;
                 const int k = k0 + kk;
-                Xs[kk][c] = (k < K) ? operand_at(bs, sx, nx, k, i0 + c) : 0.0;
-                Ys[kk][c] = (k < K) ? operand_at(bs, sy, ny, k, j0 + c) : 0.0;
+                px[e] = (k < K) ? operand_at(bs, sx, nx, k, i0 + c) : 0.0;
+                py[e] = (k < K) ? operand_at(bs, sy, ny, k, j0 + c) : 0.0;
             }
-            __syncthreads();
-            if (warp_rows) {
-                const int kmax = min(BK, K - k0);
-                const int row = warp * 8 + 2 * lr;
-                for (int kk = 0; kk < kmax; ++kk) {
-                    const double xa = Xs[kk][row], xb = Xs[kk][row + 1];
+        };
+        auto stash = [&](int buf) {
 #pragma unroll
-                    for (int bb = 0; bb < 8; ++bb) {
-                        if (bval[bb]) {
-                            const double y = Ys[kk][lc + 8 * bb];
-                            acc[0][bb] = fma(xa, y, acc[0][bb]);
-                            acc[1][bb] = fma(xb, y, acc[1][bb]);
-                        }
-                    }
+            for (int e = 0; e < LOADS; ++e) {
+                const int idx = tid + e * NTHREADS;
+                const int kk = idx / TILE, c = idx % TILE;
+                Xs[buf][kk][c] = px[e];
+                Ys[buf][kk][c] = py[e];
+            }
+        };
+
+        int buf = 0;
+        if (K > 0) {
+            fetch(0);
+            stash(0);
+        }
+        __syncthreads();
+        for (int k0 = 0; k0 < K; k0 += BK) {
+            const bool more = k0 + BK < K;
+            if (more) fetch(k0 + BK);  // global loads in flight during the slab's DFMAs
+            if (active) {
+                const int kmax = min(BK, K - k0);
+                for (int kk = 0; kk < kmax; ++kk) {
+                    const double2 xa = *reinterpret_cast<const double2*>(&Xs[buf][kk][row0]);
+                    const double2 xb = *reinterpret_cast<const double2*>(&Xs[buf][kk][row0 + 2]);
+                    const double x[4] = {xa.x, xa.y, xb.x, xb.y};
+                    double y[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) y[b] = Ys[buf][kk][col0 + 8 * b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
                 }
             }
+            if (more) stash(buf ^ 1);
             __syncthreads();
+            buf ^= 1;
         }
 
         // epilogue: dense workspace buffer, block of packed C, or upper part of a diagonal block
         const Bind& bind = bs.b[sp.inst];
-        if (warp_rows) {
+        if (active) {
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int i = i0 + warp * 8 + 2 * lr + a;
+            for (int a = 0; a < 4; ++a) {
+                const int i = i0 + row0 + a;
                 if (i >= sp.out_rows) continue;
 #pragma unroll
-                for (int bb = 0; bb < 8; ++bb) {
-                    const int j = j0 + lc + 8 * bb;
+                for (int b = 0; b < 4; ++b) {
+                    const int j = j0 + col0 + 8 * b;
                     if (j >= sp.out_cols) continue;
                     if (sp.out_kind == OUT_DENSE) {
-                        reinterpret_cast<double*>(bind.W)[sp.out_off + (int64_t)i * sp.out_ld + j] = acc[a][bb];
+                        reinterpret_cast<double*>(bind.W)[sp.out_off + (int64_t)i * sp.out_ld + j] = acc[a][b];
                     } else {
                         const int64_t gi = (int64_t)sp.ci0 + i, gj = (int64_t)sp.cj0 + j;
                         if (sp.out_kind == OUT_SYRK && gj < gi) continue;
-                        bind.C[packed_start(gi, bind.n) + (gj - gi)] = acc[a][bb];
+                        bind.C[packed_start(gi, bind.n) + (gj - gi)] = acc[a][b];
                     }
                 }
             }

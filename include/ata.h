@@ -196,6 +196,13 @@ ata_status ata_plan_enable_stage_timing(ata_plan plan, int enable);
 ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms,
                                 float* combine_ms);
 
+/* Error word of the plan's tensor-core kernels (0 = none).  Their waits on
+ * pipeline barriers are bounded (1 s); a wait that gives up records a
+ * nonzero code (1 TMA producer, 2 MMA issuer, 3 epilogue), the kernel
+ * returns without finishing, and the word stays set for the plan.
+ * Synchronises with the device.  Errors: ATA_EINVAL, ATA_ECUDA. */
+ata_status ata_plan_device_status(ata_plan plan, int* code);
+
 /* Release the plan (waits for its queued work first). */
 void ata_plan_destroy(ata_plan plan);
 

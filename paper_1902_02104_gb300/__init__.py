@@ -86,6 +86,7 @@ def load():
                                  ctypes.POINTER(vp), vp], i32),
         "ata_plan_destroy": ([vp], None),
         "ata_execute_static_scratch": ([i64, i64, vp, i64, dp, i32, vp], i32),
+        "ata_plan_device_status": ([vp, ctypes.POINTER(ctypes.c_int)], i32),
         "ata_plan_enable_stage_timing": ([vp, i32], i32),
         "ata_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_float)], i32),
@@ -160,6 +161,12 @@ class Plan:
     def in_dtype(self):
         import torch
         return torch.float64 if self.dtype in (ATA_F64, ATA_F64_OZAKI) else torch.float32
+
+    def device_status(self) -> int:
+        """Error word of the plan's tensor-core kernels (0 = none); synchronises."""
+        c = ctypes.c_int()
+        _check(load().ata_plan_device_status(self.handle, ctypes.byref(c)))
+        return c.value
 
     def enable_stage_timing(self, enable: bool = True):
         _check(load().ata_plan_enable_stage_timing(self.handle, int(enable)))

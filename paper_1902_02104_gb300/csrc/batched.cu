@@ -97,6 +97,12 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
             finalize_tables(&h, in_dt, sum_dt);
             ata_status st = upload_tables(h, &e->tables);
             if (st != ATA_OK) return st;
+            if (leaf != LEAF_F64 && !h.prods.empty()) {
+                std::vector<char*> ws;
+                for (int i = g0; i < g1; ++i) ws.push_back(plan_workspace(plans[i]));
+                st = build_tc_tables(h, ws, &e->tables);
+                if (st != ATA_OK) return st;
+            }
             it = g_batches.emplace(gkey, std::move(e)).first;
         }
         std::vector<Bind> binds;

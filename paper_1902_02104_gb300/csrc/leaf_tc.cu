@@ -1,16 +1,960 @@
-// leaf_tc.cu -- tensor-core leaf products (bf16x3 / TF32 / FP64 emulation).
+// leaf_tc.cu -- tensor-core leaf products on sm_103a (tcgen05 + TMEM + TMA).
+//
+// Three leaf arithmetics share one pipeline:
+//   bf16x3  FP32 operands, per column scaled by 2^-E (max |x| < 2^E) and cut
+//           into three signed base-256 digits, each an exact bf16 (24 bits,
+//           the FP32 significand); the six part products of order a+b <= 2.
+//   tf32    FP32 operands rounded to TF32 (kind::tf32), one product.
+//   ozaki   FP64 operands, same slicing with six digits (48 bits); the 21
+//           part products of order <= 5.  This emulates the FP64 product
+//           with bf16 tensor cores (an Ozaki-style scheme).
+// Part products are exact in FP32.  The tensor core accumulates in FP32
+// with truncation, so an accumulator that runs over a long K drifts by a
+// relative ~2^-23 per addition.  Orders whose share of the result is large
+// are therefore accumulated per K chunk of 128 in their own accumulator, in
+// which every partial sum is an integer below 2^24 units (exact), and drained
+// into float-float (hi, lo) sums by the epilogue after each chunk: orders 0-1
+// for bf16x3, 0-2 for ozaki.  The remaining orders (2 for bf16x3: ~2^-16 of
+// the result, accumulated over the whole K; 3-5 for ozaki, drained per chunk)
+// add errors far below the stated bounds.  Results are scaled back by
+// 2^(E_i + F_j) with integer exponent arithmetic and written in FP64.
+//
+// Stage 1 (operand preparation, memory bound): every leaf operand -- a signed
+// sum of blocks of A or of materialised Strassen sums -- is formed once,
+// sliced and written K-major (row = output index, K contiguous), zero padded
+// to whole 128-row tiles, so that a TMA 2D load of a (K-block x 128 rows) box
+// with 128B / 64B swizzle lands in shared memory in the canonical K-major
+// UMMA layout.  Sliced modes first reduce each column's max |x|.
+//
+// Stage 2 (persistent GEMM, one CTA per SM): warp 0 issues TMA loads of all
+// parts of a K-block into a stage ring, warp 1 issues tcgen05.mma (M = 128,
+// N = 128, FP32 accumulators in TMEM), the epilogue warps drain TMEM
+// (tcgen05.ld) and write the FP64 tile.  Every wait on an mbarrier is bounded
+// (1 s, %globaltimer); on timeout the kernel records an error code in the
+// table's status word, the other roles notice it and give up too, in-flight
+// copies and MMAs are waited for (bounded), TMEM is freed and the kernel
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
 #include "runtime.h"
 
 namespace ata {
+namespace {
 
-bool leaf_supported(LeafKind k) { return k == LEAF_F64; }
+constexpr int MODE_BF16X3 = 1, MODE_TF32 = 2, MODE_OZAKI = 3;  // == LeafKind values
+constexpr uint64_t kTimeoutNs = 1000000000ull;
+constexpr int ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE = 3;
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity.  Returns false
+// (after recording `code` in *status unless another role already did) when
+// the wait gives up: on a timeout, or when *status shows that another role
+// gave up first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*reinterpret_cast<volatile int*>(status) != 0) return false;
+            if (globaltimer() - t0 > kTimeoutNs) {
+                atomicCAS(status, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(dst),
+        "l"(tmap), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if constexpr (MODE == MODE_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Exact FP32 -> FP64 widening with integer operations (the FP64 pipe is the
+// scarce unit on this part); zero and subnormal inputs give 0, which changes
+// a result by less than 2^-126 of its unit.
+__device__ __forceinline__ long long f2d_bits(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int e = (b >> 23) & 0xFF;
+    if (e == 0) return 0;
+    return ((long long)(b >> 31) << 63) | ((long long)(e + 896) << 52) | ((long long)(b & 0x7FFFFF) << 29);
+}
+
+// Scale exponent E of a column whose largest magnitude has bit pattern mx:
+// mx = f * 2^E with f in [0.5, 1); 0 for an all-zero (or subnormal) column.
+__device__ __forceinline__ int col_exponent(unsigned long long mx) {
+    const int eb = (int)((mx >> 52) & 0x7FF);
+    return eb == 0 ? 0 : eb - 1022;
+}
+
+// K-major shared-memory matrix descriptor (tcgen05 "matrix descriptor"):
+// start address, leading byte offset (unused for swizzled K-major),
+// stride byte offset between 8-row groups, version 1, swizzle mode.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t swizzle) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)swizzle << 61;
+    return d;
+}
+
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// float-float accumulation (hi, lo) += x
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+
+__device__ __forceinline__ int64_t packed_start(int64_t i, int64_t n) { return i * n - i * (i - 1) / 2; }
+
+// ---------------------------------------------------------------------------
+// Mode geometry
+//
+// Accumulators live in TMEM, 128 columns each (one N = 128 tile):
+//   D group: exact per-chunk accumulators, order d -> accumulator d (d < ND),
+//            drained after the chunk's last K-block;
+//   F group: the other orders (FMIN..FMAX) in one accumulator, either over
+//            the whole K (F_FINAL) or drained per chunk like the D group.
+// The float-float running sums (hi, lo) of a thread's columns: hi always in
+// registers, lo in TMEM (LO_TMEM) or in registers.
+
+template <int MODE>
+struct Geo;
+
+template <>
+struct Geo<MODE_BF16X3> {
+    static constexpr int PARTS = 3, ELEM = 2, KBLK = 64, ROWB = 128, KSTEP = 16, NSTAGE = 2;
+    static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
+    static constexpr int KC = 128, ND = 2, FMIN = 2, FMAX = 2;
+    static constexpr bool F_FINAL = true, LO_TMEM = true, LO_SMEM = false, SLICED = true;
+    static constexpr int EPI_WARPS = 8;
+    static constexpr uint32_t TMEM_COLS = 512, F_COL = 256, LO_COL = 384;
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+};
+
+template <>
+struct Geo<MODE_TF32> {
+    static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6;
+    static constexpr uint32_t SWZ = 2, SBO = 1024;
+    static constexpr int KC = 1 << 30, ND = 0, FMIN = 0, FMAX = 0;
+    static constexpr bool F_FINAL = true, LO_TMEM = false, LO_SMEM = false, SLICED = false;
+    static constexpr int EPI_WARPS = 8;
+    static constexpr uint32_t TMEM_COLS = 128, F_COL = 0, LO_COL = 0;
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+};
+
+template <>
+struct Geo<MODE_OZAKI> {
+    static constexpr int PARTS = 6, ELEM = 2, KBLK = 16, ROWB = 32, KSTEP = 16, NSTAGE = 3;
+    static constexpr uint32_t SWZ = 6, SBO = 256;  // 32B swizzle
+    static constexpr int KC = 128, ND = 3, FMIN = 3, FMAX = 5;
+    static constexpr bool F_FINAL = false, LO_TMEM = false, LO_SMEM = true, SLICED = true;
+    static constexpr int EPI_WARPS = 16;
+    static constexpr uint32_t TMEM_COLS = 512, F_COL = 384, LO_COL = 0;
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+};
+
+template <int MODE>
+__host__ __device__ constexpr int tile_bytes() {
+    return 128 * Geo<MODE>::ROWB;
+}
+template <int MODE>
+__host__ __device__ constexpr int stage_bytes() {
+    return 2 * Geo<MODE>::PARTS * tile_bytes<MODE>();
+}
+template <int MODE>
+__host__ __device__ constexpr int lo_smem_bytes() {
+    return Geo<MODE>::LO_SMEM ? 128 * 128 * 4 : 0;
+}
+template <int MODE>
+__host__ __device__ constexpr int smem_bytes() {
+    return Geo<MODE>::NSTAGE * stage_bytes<MODE>() + lo_smem_bytes<MODE>() + 1024 /*align*/ + 256 /*barriers*/;
+}
+template <int MODE>
+__host__ __device__ constexpr int threads_of() {
+    return 32 * (2 + Geo<MODE>::EPI_WARPS);
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation
+
+template <typename TS, int NB>
+__device__ __forceinline__ TS operand_value(const BindSet<NB>& bs, const Term* ts, int t0, int nt, int k, int c) {
+    TS v = 0;
+    for (int t = 0; t < nt; ++t) {
+        const Term& tm = ts[t0 + t];
+        if (k < tm.rows && c < tm.cols) {
+            const Bind& b = bs.b[tm.inst];
+            const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
+            const TS x = __ldg(base + tm.off + (int64_t)k * tm.ld + c);
+            v = tm.neg ? v - x : v + x;
+        }
+    }
+    return v;
+}
+
+// Column maxima of |operand| (sliced modes): atomicMax on the FP64 bit
+// pattern (positive doubles order like their bits).  Block: a 64 (K) x 32
+// (column) tile.
+template <int NB, typename TS>
+__global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                        const LeafProduct* __restrict__ prods,
+                                                        const Term* __restrict__ terms,
+                                                        const TcProd* __restrict__ tcp,
+                                                        const PrepTask* __restrict__ tasks) {
+    __shared__ double red[8][32];
+    const PrepTask tk = tasks[blockIdx.x];
+    const LeafProduct& lp = prods[tk.prod];
+    const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
+    const int col = threadIdx.x & 31, kr = threadIdx.x >> 5;
+    const int c = tk.c0 + col;
+    double m = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int k = tk.k0 + kr + 8 * u;
+        if (k < lp.K) m = fmax(m, (double)fabs(operand_value<TS>(bs, terms, t0, nt, k, c)));
+    }
+    red[kr][col] = m;
+    __syncthreads();
+    if (kr == 0) {
+        for (int i = 1; i < 8; ++i) m = fmax(m, red[i][col]);
+        unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
+        if (m > 0.0) atomicMax(ex + c, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// Balanced base-256 digits of round(x * 2^(8S - E)), most significant first:
+// x * 2^-E ~= sum_s d[s] * 2^(-8(s+1)), |d[0]| <= 256, |d[s>0]| <= 128.
+// Integer arithmetic only (the FP64 pipe is not involved).
+template <int S>
+__device__ __forceinline__ void slice_digits(double x, int E, int (&d)[S]) {
+    const long long bits = __double_as_longlong(x);
+    const int eb = (int)((bits >> 52) & 0x7FF);
+    long long v = 0;
+    if (eb != 0 && eb != 0x7FF) {
+        const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+        const int shift = (eb - 1075) + 8 * S - E;
+        if (shift >= 0)
+            v = m << shift;
+        else if (shift > -62)
+            v = (m + (1LL << (-shift - 1))) >> (-shift);
+        if (bits < 0) v = -v;
+    }
+#pragma unroll
+    for (int s = S - 1; s >= 1; --s) {
+        const long long r = ((v + 128) & 255) - 128;
+        d[s] = (int)r;
+        v = (v - r) >> 8;
+    }
+    d[0] = (int)v;
+}
+
+template <int MODE>
+struct PrepSrc {
+    using T = float;
+};
+template <>
+struct PrepSrc<MODE_OZAKI> {
+    using T = double;
+};
+
+// Parts of one 64 (K) x 32 (column) tile of a leaf operand, written K-major:
+// part q of column c, K index k at parts + ((q * rows_pad + c) * K_pad + k).
+template <int NB, int MODE>
+__global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                      const LeafProduct* __restrict__ prods,
+                                                      const Term* __restrict__ terms,
+                                                      const TcProd* __restrict__ tcp,
+                                                      const PrepTask* __restrict__ tasks) {
+    using TS = typename PrepSrc<MODE>::T;
+    __shared__ TS tile[64][33];
+    const PrepTask tk = tasks[blockIdx.x];
+    const LeafProduct& lp = prods[tk.prod];
+    const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
+    {
+        const int col = threadIdx.x & 31, kr = threadIdx.x >> 5;
+        const int c = tk.c0 + col;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kk = kr + 8 * u, k = tk.k0 + kk;
+            tile[kk][col] = (k < lp.K) ? operand_value<TS>(bs, terms, t0, nt, k, c) : TS(0);
+        }
+    }
+    __syncthreads();
+    const int col = threadIdx.x >> 3, kc = threadIdx.x & 7;
+    const int c = tk.c0 + col;
+    const int rows_pad = tk.side ? lp.r_pad : lp.p_pad;
+    const Bind& b = bs.b[lp.inst];
+    char* parts = b.W + (tk.side ? lp.tc_y_off : lp.tc_x_off);
+    const int64_t part_elems = (int64_t)rows_pad * lp.K_pad;
+    const int64_t base = (int64_t)c * lp.K_pad + tk.k0 + kc * 8;
+    if constexpr (MODE == MODE_TF32) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            uint32_t r;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(tile[kc * 8 + i][col]));
+            v[i] = __uint_as_float(r);
+        }
+        float* out = reinterpret_cast<float*>(parts);
+        *reinterpret_cast<uint4*>(out + base) = *reinterpret_cast<const uint4*>(v);
+        *reinterpret_cast<uint4*>(out + base + 4) = *reinterpret_cast<const uint4*>(v + 4);
+    } else {
+        constexpr int S = Geo<MODE>::PARTS;
+        const unsigned long long mx =
+            reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
+        const int E = col_exponent(mx);
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            __nv_bfloat16 q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                int d[S];
+                slice_digits<S>((double)tile[kc * 8 + i][col], E, d);
+                q[i] = __float2bfloat16_rn(__int2float_rn(d[s]) * __int_as_float((127 - 8 * (s + 1)) << 23));
+            }
+            *reinterpret_cast<uint4*>(out + s * part_elems + base) = *reinterpret_cast<const uint4*>(q);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent tcgen05 GEMM over leaf tiles
+
+template <int NB, int MODE>
+__global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                                       const TcProd* __restrict__ tcp,
+                                                                       const LeafTile* __restrict__ tiles,
+                                                                       int ntiles, int* __restrict__ status) {
+    using G = Geo<MODE>;
+    constexpr int NCOL = 128 / (G::EPI_WARPS / 4);  // columns per epilogue thread
+    constexpr int NG = NCOL / 16;                   // 16-column groups per thread
+    constexpr int kbpc = G::KC / G::KBLK > 0 ? G::KC / G::KBLK : 1;
+    constexpr bool HAS_F = true;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* lo_s = reinterpret_cast<float*>(smem + G::NSTAGE * stage_bytes<MODE>());  // [col][row] (LO_SMEM)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * stage_bytes<MODE>() + lo_smem_bytes<MODE>());
+    // barriers: full[NSTAGE] empty[NSTAGE] dfull dempty ffull fempty done ; tmem slot
+    const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * G::NSTAGE;
+    const uint32_t b_dfull = b_empty + 8 * G::NSTAGE, b_dempty = b_dfull + 8;
+    const uint32_t b_ffull = b_dempty + 8, b_fempty = b_ffull + 8, b_done = b_fempty + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * G::NSTAGE + 5);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G::NSTAGE; ++s) {
+            mbar_init(b_full + 8 * s, 1);
+            mbar_init(b_empty + 8 * s, 1);
+        }
+        mbar_init(b_dfull, 1);
+        mbar_init(b_dempty, G::EPI_WARPS);
+        mbar_init(b_ffull, 1);
+        mbar_init(b_fempty, G::EPI_WARPS);
+        mbar_init(b_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), G::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t smem_base = smem_u32(smem);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const LeafTile lt = tiles[t];
+                const TcProd* pr = tcp + lt.prod;
+                const int nkb = pr->K_pad / G::KBLK;
+                const int ya = lt.ti * 128, yb = lt.tj * 128;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % G::NSTAGE, ph = (it / G::NSTAGE) & 1;
+                    if (!mbar_wait(b_empty + 8 * s, ph ^ 1, status, ERR_TIMEOUT_PRODUCER)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(b_full + 8 * s, stage_bytes<MODE>());
+                    const uint32_t st = smem_base + s * stage_bytes<MODE>();
+#pragma unroll
+                    for (int q = 0; q < G::PARTS; ++q) {
+                        tma_load_2d(st + q * tile_bytes<MODE>(), &pr->tmx, b_full + 8 * s, kb * G::KBLK,
+                                    q * pr->p_pad + ya);
+                        tma_load_2d(st + (G::PARTS + q) * tile_bytes<MODE>(), &pr->tmy, b_full + 8 * s,
+                                    kb * G::KBLK, q * pr->r_pad + yb);
+                    }
+                }
+            }
+            // copies still in flight land before the CTA may exit (bounded)
+            const uint32_t n_in_flight = it < (uint32_t)G::NSTAGE ? it : (uint32_t)G::NSTAGE;
+            for (uint32_t j = 0; j < n_in_flight; ++j) {
+                const uint32_t i2 = it - 1 - j;
+                const uint32_t s = i2 % G::NSTAGE, ph = (i2 / G::NSTAGE) & 1;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(b_full + 8 * s, ph) && globaltimer() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, chunk = 0, tcount = 0;
+            bool ok = true;
+            constexpr int NKS = G::KBLK / G::KSTEP;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+                const LeafTile lt = tiles[t];
+                const int nkb = tcp[lt.prod].K_pad / G::KBLK;
+                if constexpr (G::F_FINAL) {
+                    if (!mbar_wait(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const bool first_in_chunk = (kb % kbpc) == 0;
+                    const bool last_in_chunk = (kb % kbpc) == kbpc - 1 || kb == nkb - 1;
+                    const uint32_t cpar = ((chunk & 1) ^ 1);
+                    if (G::ND > 0 && first_in_chunk) {
+                        if (!mbar_wait(b_dempty, cpar, status, ERR_TIMEOUT_MMA)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    const uint32_t s = it % G::NSTAGE, ph = (it / G::NSTAGE) & 1;
+                    if (!mbar_wait(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_base + s * stage_bytes<MODE>();
+                    auto desc_a = [&](int q, int ks) {
+                        return make_desc(st + q * tile_bytes<MODE>() + ks * G::KSTEP * G::ELEM, G::SBO, G::SWZ);
+                    };
+                    auto desc_b = [&](int q, int ks) {
+                        return make_desc(st + (G::PARTS + q) * tile_bytes<MODE>() + ks * G::KSTEP * G::ELEM, G::SBO,
+                                         G::SWZ);
+                    };
+                    // D group: order d into accumulator d, overwritten at the chunk's start
+#pragma unroll
+                    for (int ord = 0; ord < G::ND; ++ord) {
+                        bool first = first_in_chunk;
+#pragma unroll
+                        for (int a = 0; a <= ord; ++a)
+#pragma unroll
+                            for (int ks = 0; ks < NKS; ++ks) {
+                                umma<MODE>(tmem + ord * 128, desc_a(a, ks), desc_b(ord - a, ks), G::IDESC,
+                                           first ? 0u : 1u);
+                                first = false;
+                            }
+                    }
+                    if (G::ND > 0 && last_in_chunk) umma_commit(b_dfull);
+                    // F group
+                    if constexpr (!G::F_FINAL) {
+                        if (first_in_chunk && !mbar_wait(b_fempty, cpar, status, ERR_TIMEOUT_MMA)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    {
+                        bool first = G::F_FINAL ? (kb == 0) : first_in_chunk;
+#pragma unroll
+                        for (int ord = G::FMIN; ord <= G::FMAX; ++ord)
+#pragma unroll
+                            for (int a = 0; a <= ord; ++a) {
+                                if (a >= G::PARTS || ord - a >= G::PARTS) continue;
+#pragma unroll
+                                for (int ks = 0; ks < NKS; ++ks) {
+                                    umma<MODE>(tmem + G::F_COL, desc_a(a, ks), desc_b(ord - a, ks), G::IDESC,
+                                               first ? 0u : 1u);
+                                    first = false;
+                                }
+                            }
+                    }
+                    if (!G::F_FINAL && last_in_chunk) umma_commit(b_ffull);
+                    umma_commit(b_empty + 8 * s);  // stage reusable once these MMAs finish
+                    if (last_in_chunk) ++chunk;
+                }
+                if (!ok) break;
+                if constexpr (G::F_FINAL) umma_commit(b_ffull);
+            }
+            // every issued MMA completes before TMEM is released (bounded)
+            umma_commit(b_done);
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(b_done, 0) && globaltimer() - t0 < kTimeoutNs) {
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        // Thread = one row (TMEM lane) of the tile and NCOL of its columns.
+        const int e = warp - 2;
+        const int q = warp & 3;              // TMEM lane quarter of this warp
+        const int cq = e >> 2;               // column slice
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        uint32_t chunk = 0, tcount = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+            const LeafTile lt = tiles[t];
+            const TcProd* pr = tcp + lt.prod;
+            const int nkb = pr->K_pad / G::KBLK;
+            const int nchunks = (nkb + kbpc - 1) / kbpc;
+            float hi[NCOL];
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) hi[c] = 0.f;
+            const int row = 32 * q + lane;
+            // drains one accumulator (TMEM column base) into (hi, lo)
+            auto drain = [&](uint32_t acc_col, bool first_chunk) {
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + acc_col + cq * NCOL + g * 16, v);
+                    if constexpr (G::LO_TMEM) {
+                        const uint32_t lo_addr = tmem + lane_base + G::LO_COL + cq * NCOL + g * 16;
+                        float lo[16];
+                        if (first_chunk) {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) lo[c] = 0.f;
+                        } else {
+                            tmem_ld16(lo_addr, lo);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) ff_add(hi[g * 16 + c], lo[c], v[c]);
+                        tmem_st16(lo_addr, lo);
+                    } else if constexpr (G::LO_SMEM) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            float* lp = lo_s + (cq * NCOL + g * 16 + c) * 128 + row;
+                            float lo = first_chunk ? 0.f : *lp;
+                            ff_add(hi[g * 16 + c], lo, v[c]);
+                            *lp = lo;
+                        }
+                    }
+                }
+            };
+            if constexpr (G::ND > 0) {
+                for (int ci = 0; ci < nchunks; ++ci, ++chunk) {
+                    if (!mbar_wait(b_dfull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int acc = 0; acc < G::ND; ++acc) drain(acc * 128, ci == 0 && acc == 0);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(b_dempty);
+                    if constexpr (!G::F_FINAL) {
+                        if (!mbar_wait(b_ffull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        drain(G::F_COL, false);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(b_fempty);
+                    }
+                }
+                if (!ok) break;
+            }
+            if constexpr (G::F_FINAL) {
+                if (!mbar_wait(b_ffull, tcount & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+            }
+            // FP64 tile: row i of this thread, NCOL columns in groups of 16
+            const Bind& bind = bs.b[pr->inst];
+            const int i = lt.ti * 128 + 32 * q + lane;
+            const int j0 = lt.tj * 128 + cq * NCOL;
+            const bool row_ok = i < pr->out_rows;
+            int Ei = 0;
+            if constexpr (G::SLICED) {
+                if (row_ok) Ei = col_exponent(reinterpret_cast<const unsigned long long*>(pr->ex)[i]);
+            }
+            double* dense = reinterpret_cast<double*>(bind.W) + pr->out_off + (int64_t)i * pr->out_ld;
+            const int64_t gi = (int64_t)pr->ci0 + i;
+            double* prow = bind.C + (packed_start(gi, bind.n) - gi + pr->cj0);
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                float lo[16], f[16];
+                if constexpr (G::LO_TMEM) {
+                    tmem_ld16(tmem + lane_base + G::LO_COL + cq * NCOL + g * 16, lo);
+                } else if constexpr (G::LO_SMEM) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) lo[c] = lo_s[(cq * NCOL + g * 16 + c) * 128 + row];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) lo[c] = 0.f;
+                }
+                if constexpr (G::F_FINAL) {
+                    tmem_ld16(tmem + lane_base + G::F_COL + cq * NCOL + g * 16, f);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) f[c] = 0.f;
+                }
+                if (row_ok) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = j0 + g * 16 + c;
+                        if (j < pr->out_cols) {
+                            float hh = hi[g * 16 + c], ll = lo[c];
+                            ff_add(hh, ll, f[c]);
+                            long long bh = f2d_bits(hh), bl = f2d_bits(ll);
+                            if constexpr (G::SLICED) {
+                                const int sc = Ei + col_exponent(reinterpret_cast<const unsigned long long*>(pr->ey)[j]);
+                                if (bh) bh += (long long)sc << 52;
+                                if (bl) bl += (long long)sc << 52;
+                            }
+                            const double v = __longlong_as_double(bh) + __longlong_as_double(bl);
+                            if (pr->out_kind == OUT_DENSE) {
+                                dense[j] = v;
+                            } else if (pr->out_kind == OUT_PACKED || (int64_t)pr->cj0 + j >= gi) {
+                                prow[j] = v;
+                            }
+                        }
+                    }
+                }
+            }
+            if constexpr (G::F_FINAL) {
+                // accumulators read: TMEM may be refilled by the next tile
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_fempty);
+            }
+        }
+    }
+
+    // teardown: every role has stopped issuing and every MMA has completed
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, G::TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <int MODE>
+bool encode_parts(CUtensorMap* map, char* base, int parts, int rows_pad, int K_pad) {
+    using G = Geo<MODE>;
+    auto enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)parts * rows_pad};
+    const cuuint64_t strides[1] = {(cuuint64_t)K_pad * G::ELEM};
+    const cuuint32_t box[2] = {(cuuint32_t)G::KBLK, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt =
+        G::ELEM == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUtensorMapSwizzle sw = G::ROWB == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : G::ROWB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                  : CU_TENSOR_MAP_SWIZZLE_32B;
+    return enc(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_for(LeafKind k, CUtensorMap* map, char* base, int rows_pad, int K_pad) {
+    switch (k) {
+        case LEAF_BF16X3: return encode_parts<MODE_BF16X3>(map, base, 3, rows_pad, K_pad);
+        case LEAF_TF32: return encode_parts<MODE_TF32>(map, base, 1, rows_pad, K_pad);
+        case LEAF_OZAKI: return encode_parts<MODE_OZAKI>(map, base, 6, rows_pad, K_pad);
+        default: return false;
+    }
+}
+
+int g_sms = 1;  // SM count of the device (set before any capture)
+
+template <int NB, int MODE>
+cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s) {
+    if (Geo<MODE>::SLICED) {
+        cudaError_t e = cudaMemsetAsync(t.tc_ex, 0, t.tc_ex_bytes, s);
+        if (e != cudaSuccess) return e;
+        if (t.nprep > 0)
+            tc_colmax_kernel<NB, typename PrepSrc<MODE>::T><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
+    }
+    if (t.nprep > 0) tc_prep_kernel<NB, MODE><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
+    const int grid = std::max(1, std::min(t.ntiles, g_sms));
+    tc_gemm_kernel<NB, MODE><<<grid, threads_of<MODE>(), smem_bytes<MODE>(), s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status);
+    return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t launch_kind(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s) {
+    switch (t.leaf) {
+        case LEAF_BF16X3: return launch_mode<NB, MODE_BF16X3>(t, bs, s);
+        case LEAF_TF32: return launch_mode<NB, MODE_TF32>(t, bs, s);
+        case LEAF_OZAKI: return launch_mode<NB, MODE_OZAKI>(t, bs, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NB, int MODE>
+cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(tc_gemm_kernel<NB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_bytes<MODE>());
+}
+
+}  // namespace
+
+bool leaf_supported(LeafKind k) {
+    return k == LEAF_F64 || k == LEAF_BF16X3 || k == LEAF_TF32 || k == LEAF_OZAKI;
+}
+
+ata_status tc_prepare_device() {
+    static cudaError_t err = cudaErrorNotReady;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        err = set_smem_attr<1, MODE_BF16X3>();
+        if (err == cudaSuccess) err = set_smem_attr<1, MODE_TF32>();
+        if (err == cudaSuccess) err = set_smem_attr<1, MODE_OZAKI>();
+        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_BF16X3>();
+        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_TF32>();
+        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_OZAKI>();
+        if (err == cudaSuccess && !get_encode()) err = cudaErrorNotSupported;
+        if (err == cudaSuccess) {
+            int dev = 0;
+            err = cudaGetDevice(&dev);
+            if (err == cudaSuccess) err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+            if (g_sms <= 0) g_sms = 1;
+        }
+    });
+    if (err != cudaSuccess) return cuda_fail(err, "tensor-core leaf set-up");
+    return ATA_OK;
+}
+
+ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d) {
+    ata_status st = tc_prepare_device();
+    if (st != ATA_OK) return st;
+    const int np = (int)h.prods.size();
+    std::vector<TcProd> tp(np);
+    std::vector<PrepTask> prep;
+    int64_t ex_elems = 0;
+    for (int i = 0; i < np; ++i) {
+        const LeafProduct& lp = h.prods[i];
+        TcProd& t = tp[i];
+        std::memset(&t, 0, sizeof(t));
+        char* W = ws[lp.inst];
+        if (!encode_for(h.leaf, &t.tmx, W + lp.tc_x_off, lp.p_pad, lp.K_pad) ||
+            !encode_for(h.leaf, &t.tmy, W + lp.tc_y_off, lp.r_pad, lp.K_pad))
+            return fail(ATA_ECUDA, "cuTensorMapEncodeTiled failed for a leaf operand");
+        t.p_pad = lp.p_pad;
+        t.r_pad = lp.r_pad;
+        t.K_pad = lp.K_pad;
+        t.inst = lp.inst;
+        t.out_rows = lp.out_rows;
+        t.out_cols = lp.out_cols;
+        t.out_kind = lp.out_kind;
+        t.out_ld = lp.out_ld;
+        t.out_off = lp.out_off;
+        t.ci0 = lp.ci0;
+        t.cj0 = lp.cj0;
+        t.ex_index = ex_elems;
+        ex_elems += lp.p_pad;
+        const bool syrk = lp.out_kind == OUT_SYRK;
+        t.ey_index = syrk ? t.ex_index : ex_elems;
+        if (!syrk) ex_elems += lp.r_pad;
+        for (int side = 0; side < (syrk ? 1 : 2); ++side) {
+            const int rows_pad = side ? lp.r_pad : lp.p_pad;
+            for (int c0 = 0; c0 < rows_pad; c0 += 32)
+                for (int k0 = 0; k0 < lp.K_pad; k0 += 64) {
+                    PrepTask pt;
+                    pt.prod = i;
+                    pt.side = (int8_t)side;
+                    pt.c0 = c0;
+                    pt.k0 = k0;
+                    prep.push_back(pt);
+                }
+        }
+    }
+    // device blob: TcProd[] | PrepTask[] | status | exponent maxima
+    auto al = [](int64_t x) { return (x + 255) / 256 * 256; };
+    const int64_t o_tp = 0;
+    const int64_t o_prep = al(o_tp + (int64_t)np * sizeof(TcProd));
+    const int64_t o_status = al(o_prep + (int64_t)prep.size() * sizeof(PrepTask));
+    const int64_t o_ex = al(o_status + 256);
+    const int64_t total = al(o_ex + std::max<int64_t>(ex_elems, 1) * 8);
+    char* blob = nullptr;
+    if (cudaMalloc(&blob, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ATA_ENOMEM, "tensor-core tables: cudaMalloc failed");
+    }
+    for (TcProd& t : tp) {
+        t.ex = reinterpret_cast<uint64_t*>(blob + o_ex) + t.ex_index;
+        t.ey = reinterpret_cast<uint64_t*>(blob + o_ex) + t.ey_index;
+    }
+    std::vector<char> hb(total, 0);
+    if (np) std::memcpy(hb.data() + o_tp, tp.data(), np * sizeof(TcProd));
+    if (!prep.empty()) std::memcpy(hb.data() + o_prep, prep.data(), prep.size() * sizeof(PrepTask));
+    cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(blob);
+        return cuda_fail(e, "tensor-core tables: upload");
+    }
+    d->tc_blob = blob;
+    d->tcp = reinterpret_cast<TcProd*>(blob + o_tp);
+    d->prep = reinterpret_cast<PrepTask*>(blob + o_prep);
+    d->nprep = (int)prep.size();
+    d->status = reinterpret_cast<int*>(blob + o_status);
+    d->tc_ex = blob + o_ex;
+    d->tc_ex_bytes = (size_t)std::max<int64_t>(ex_elems, 1) * 8;
+    return ATA_OK;
+}
 
 ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s) {
-    (void)t;
-    (void)binds;
-    (void)nb;
-    (void)s;
-    return fail(ATA_EUNSUPPORTED, "tensor-core leaves are not built into this library");
+    cudaError_t e;
+    if (nb <= 1) {
+        BindSet<1> bs{};
+        bs.b[0] = binds[0];
+        e = launch_kind<1>(t, bs, s);
+    } else if (nb <= kMaxBatchBind) {
+        BindSet<kMaxBatchBind> bs{};
+        for (int i = 0; i < nb; ++i) bs.b[i] = binds[i];
+        e = launch_kind<kMaxBatchBind>(t, bs, s);
+    } else {
+        return fail(ATA_EINVAL, "too many instances in one launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core leaf launch");
+    return ATA_OK;
 }
 
 }  // namespace ata

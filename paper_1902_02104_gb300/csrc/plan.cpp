@@ -139,6 +139,15 @@ void emit_leaf(Ctx& c, const std::vector<Term>& X, const std::vector<Term>& Y, i
     lp.out_cols = (int32_t)out_cols;
     lp.x_dt = x_dt;
     lp.y_dt = y_dt;
+    if (P.leaf != LEAF_F64) {
+        // split parts of both operands, K-major, zero padded to whole tiles
+        const TcGeom g = tc_geom(P.leaf);
+        lp.p_pad = (int32_t)((p + kTcTile - 1) / kTcTile * kTcTile);
+        lp.r_pad = (int32_t)((r + kTcTile - 1) / kTcTile * kTcTile);
+        lp.K_pad = (int32_t)std::max<int64_t>((K + g.k_align - 1) / g.k_align * g.k_align, g.k_align);
+        lp.tc_x_off = c.alloc((int64_t)g.parts * lp.p_pad * lp.K_pad * g.elem);
+        lp.tc_y_off = syrk ? lp.tc_x_off : c.alloc((int64_t)g.parts * lp.r_pad * lp.K_pad * g.elem);
+    }
     if (syrk) {
         lp.out_kind = OUT_SYRK;
         lp.ci0 = out.ci0;
@@ -153,10 +162,16 @@ void emit_leaf(Ctx& c, const std::vector<Term>& X, const std::vector<Term>& Y, i
         lp.work = p * r * K;
     }
     P.stats.mults += lp.work;
-    // operand sums recomputed per tile by fused loads (64-wide tiles)
-    const int64_t tiles_r = (r + 63) / 64, tiles_p = (p + 63) / 64;
-    if (lp.nx > 1) P.stats.adds += (int64_t)(lp.nx - 1) * K * p * tiles_r;
-    if (lp.ny > 1) P.stats.adds += (int64_t)(lp.ny - 1) * K * r * tiles_p;
+    if (P.leaf == LEAF_F64) {
+        // operand sums recomputed per tile by fused loads (64-wide tiles)
+        const int64_t tiles_r = (r + 63) / 64, tiles_p = (p + 63) / 64;
+        if (lp.nx > 1) P.stats.adds += (int64_t)(lp.nx - 1) * K * p * tiles_r;
+        if (lp.ny > 1) P.stats.adds += (int64_t)(lp.ny - 1) * K * r * tiles_p;
+    } else {
+        // fused sums are formed once per element by the operand preparation
+        if (lp.nx > 1) P.stats.adds += (int64_t)(lp.nx - 1) * K * p;
+        if (lp.ny > 1) P.stats.adds += (int64_t)(lp.ny - 1) * K * r;
+    }
     P.products.push_back(lp);
 }
 
@@ -188,7 +203,10 @@ void expand(Ctx& c, const std::vector<Term>& X, const std::vector<Term>& Y, int6
         const int8_t parent_dt = side == 0 ? x_dt : y_dt;
         int sum_slot[7];
         for (int i = 0; i < 7; ++i) sum_slot[i] = -1;
-        if (mat) {
+        if (mat && parent.empty()) {
+            // an all-padding operand: every child operand is zero as well
+            for (int i = 0; i < 7; ++i) cdt[side][i] = parent_dt;
+        } else if (mat) {
             // the parent operand is a single term here (a block of A or a
             // materialised buffer); one split task writes every sum
             SplitTask st{};
@@ -303,6 +321,15 @@ void recurse_columns(Ctx& c, int64_t c0, int64_t w, int depth) {
 }
 
 }  // namespace
+
+TcGeom tc_geom(LeafKind k) {
+    switch (k) {
+        case LEAF_BF16X3: return {3, 2, 64};
+        case LEAF_TF32: return {1, 4, 64};
+        case LEAF_OZAKI: return {6, 2, 64};
+        default: return {0, 8, 1};
+    }
+}
 
 int64_t leaf_tiles(const LeafProduct& p, int tm, int tn) {
     const int64_t a = (p.out_rows + tm - 1) / tm, b = (p.out_cols + tn - 1) / tn;

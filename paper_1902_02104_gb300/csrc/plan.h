@@ -66,6 +66,10 @@ struct LeafProduct {
     int64_t work;             // scalar multiplications (for ordering and stats)
     int32_t inst;             // instance of a batched execution (0 for one plan)
     int32_t pad2_;
+    // tensor-core leaves: split operand parts, K-major, in W (byte offsets)
+    int64_t tc_x_off, tc_y_off;   // parts x rows_pad x K_pad elements each
+    int32_t p_pad, r_pad, K_pad;  // rows of X / Y parts (multiples of 128), K padded
+    int32_t pad3_;
 };
 
 // Split task: one operand block (K x c, single term `src`) -> child sums.
@@ -118,6 +122,15 @@ struct Plan {
     int64_t ws_bytes = 0;
     PlanStats stats;
 };
+
+// Tensor-core leaf geometry per leaf kind.
+struct TcGeom {
+    int parts;       // split parts per operand
+    int elem;        // bytes per part element (2: bf16, 4: tf32 as fp32)
+    int k_align;     // K padding of part buffers (elements)
+};
+TcGeom tc_geom(LeafKind k);
+constexpr int kTcTile = 128;  // tensor-core leaf tile (rows and columns)
 
 struct PlanOptions {
     int cutoff = 64;

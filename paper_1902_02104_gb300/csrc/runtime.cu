@@ -133,7 +133,7 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h) {
     }
     for (size_t i = 0; i < P.products.size(); ++i) {
         const LeafProduct& lp = P.products[i];
-        const int tm = kF64Tile;
+        const int tm = leaf_tile(P.leaf);
         const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tm - 1) / tm;
         for (int64_t ti = 0; ti < a; ++ti)
             for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti : 0); tj < b; ++tj) {
@@ -192,9 +192,16 @@ void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt) {
     h->comb_pending.clear();
 }
 
+int leaf_tile(LeafKind k) { return k == LEAF_F64 ? kF64Tile : kTcTile; }
+
 void DeviceTables::free_all() {
     if (blob) cudaFree(blob);
+    if (tc_blob) cudaFree(tc_blob);
     blob = nullptr;
+    tc_blob = nullptr;
+    tcp = nullptr;
+    prep = nullptr;
+    status = nullptr;
 }
 
 // Queues one execution of `t` with bindings `binds` on `s` (no graph).
@@ -395,7 +402,7 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     out->max_strassen_levels = P.stats.max_strassen_levels;
     out->n_leaf_products = (int32_t)P.products.size();
     int64_t tiles = 0;
-    for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, kF64Tile, kF64Tile);
+    for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, leaf_tile(P.leaf), leaf_tile(P.leaf));
     out->n_leaf_tiles = (int32_t)tiles;
     int64_t ns = 0, nc = 0;
     for (auto& v : P.split_levels) ns += v.size();
@@ -425,6 +432,10 @@ ata_status rebuild_tables(ata_plan plan, int64_t lda) {
     finalize_tables(&h, plan->plan.in_dt, plan->plan.sum_dt);
     ata_status st = upload_tables(h, &plan->tables);
     if (st != ATA_OK) return st;
+    if (plan->plan.leaf != LEAF_F64 && !h.prods.empty()) {
+        st = build_tc_tables(h, std::vector<char*>{plan->ws}, &plan->tables);
+        if (st != ATA_OK) return st;
+    }
     plan->lda = lda;
     plan->graph.release();
     return ATA_OK;
@@ -605,6 +616,14 @@ ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms, 
     ATA_CUDA(cudaEventElapsedTime(split_ms, plan->graph.ev[0], plan->graph.ev[1]));
     ATA_CUDA(cudaEventElapsedTime(leaf_ms, plan->graph.ev[1], plan->graph.ev[2]));
     ATA_CUDA(cudaEventElapsedTime(combine_ms, plan->graph.ev[2], plan->graph.ev[3]));
+    return ATA_OK;
+}
+
+ata_status ata_plan_device_status(ata_plan plan, int* code) {
+    if (!plan || !code) return fail(ATA_EINVAL, "NULL argument");
+    *code = 0;
+    if (!plan->tables.status) return ATA_OK;
+    ATA_CUDA(cudaMemcpy(code, plan->tables.status, sizeof(int), cudaMemcpyDeviceToHost));
     return ATA_OK;
 }
 

@@ -1,5 +1,6 @@
 // runtime.h -- internal runtime types shared by the C-ABI translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <map>
@@ -16,6 +17,27 @@ namespace ata {
 struct LevelRange {
     int32_t chunk0 = 0, nchunks = 0;
     int8_t src_dt = DT_F64, dst_dt = DT_F64;
+};
+
+// Tensor-core leaf product as the GEMM kernel sees it: TMA maps of the split
+// parts of both operands (parts stacked along rows) and the output target.
+struct alignas(64) TcProd {
+    CUtensorMap tmx;
+    CUtensorMap tmy;
+    int32_t p_pad, r_pad, K_pad, inst;
+    int32_t out_rows, out_cols, out_kind, out_ld;
+    int64_t out_off;
+    int32_t ci0, cj0;
+    uint64_t* ex;      // FP64 emulation: max |x| per row of X (bit patterns)
+    uint64_t* ey;      // ... per row of Y
+    int64_t ex_index, ey_index;
+};
+
+// One 64 (K) x 32 (column) tile of a leaf operand for the preparation kernels.
+struct PrepTask {
+    int32_t prod;
+    int8_t side, pad_[3];
+    int32_t c0, k0;
 };
 
 // Task tables on the host, ready to upload (one plan or a merged batch).
@@ -49,6 +71,14 @@ struct DeviceTables {
     CombineTask* comb = nullptr;
     Chunk* comb_chunks = nullptr;
     std::vector<LevelRange> comb_lv;
+    // tensor-core leaves
+    char* tc_blob = nullptr;
+    TcProd* tcp = nullptr;
+    PrepTask* prep = nullptr;
+    int nprep = 0;
+    int* status = nullptr;     // device error word of the tensor-core kernels
+    char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
+    size_t tc_ex_bytes = 0;
     void free_all();
 };
 
@@ -77,7 +107,9 @@ ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, Gr
 
 // Tensor-core leaf launch (bf16x3 / TF32 / FP64 emulation).
 ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s);
+ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d);
 bool leaf_supported(LeafKind k);
+int leaf_tile(LeafKind k);
 
 // Planner defaults and the autotuner.
 int default_cutoff(int64_t m, int64_t n, ata_dtype dtype);

@@ -1,0 +1,156 @@
+"""Parity of the tensor-core leaves (bf16x3, TF32, FP64 emulation) with the
+oracle, through the C ABI.
+
+Tolerances (BASELINE config 3): normwise ||C - C_ref||_F / ||C_ref||_F <=
+1e-6 for bf16x3 and <= 1e-3 for TF32, where C_ref is the FP64 product of the
+FP32-rounded input; the FP64-emulation leaf (ATA_F64_OZAKI) keeps the FP64
+componentwise bound max |C - C_ref| / (|A|^t|A|) <= 1e-11.
+Exact-integer inputs must match bitwise in every mode: bf16 holds integers
+up to 256 exactly, TF32 up to 2048, and all partial sums stay below 2^24.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1902_02104_gb300 as ata
+from paper_1902_02104_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+NORM_TOL = {ata.ATA_F32_BF16X3: 1e-6, ata.ATA_F32_TF32: 1e-3}
+MODES32 = [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32]
+
+
+def run(A_np, dtype, cutoff, **opts):
+    import torch
+    m, n = A_np.shape
+    plan = ata.Plan(m, n, dtype, cutoff, **opts)
+    A = torch.from_numpy(np.ascontiguousarray(A_np)).cuda()
+    C = plan(A)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    return C.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("dtype", [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI])
+def test_single_tile_integers(gpu, dtype):
+    # one diagonal leaf of 100 columns, K = 200: one 128 x 128 tile
+    A = inputs.integers(200, 100, seed=1).astype(np.float64 if dtype == ata.ATA_F64_OZAKI else np.float32)
+    C, _ = run(A, dtype, 4096)
+    assert np.array_equal(C, oracle.ata_packed(A))
+
+
+@pytest.mark.parametrize("dtype", [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI])
+@pytest.mark.parametrize("m,n,cutoff,fuse", [(700, 300, 64, 0), (700, 300, 64, 1), (1000, 520, 128, 1),
+                                             (129, 400, 32, 0), (1500, 257, 64, 0)])
+def test_exact_integers_bitwise(gpu, dtype, m, n, cutoff, fuse):
+    dt = np.float64 if dtype == ata.ATA_F64_OZAKI else np.float32
+    A = inputs.integers(m, n, seed=m + n).astype(dt)
+    C, _ = run(A, dtype, cutoff, fuse_levels=fuse)
+    assert np.array_equal(C, oracle.ata_packed(A))
+
+
+@pytest.mark.parametrize("dtype", MODES32)
+@pytest.mark.parametrize("m,n,cutoff", [(1500, 700, 256), (3000, 1030, 512), (333, 1111, 128)])
+def test_fp32_modes_normwise(gpu, dtype, m, n, cutoff):
+    A = inputs.normal(m, n, seed=7, dtype=np.float32)
+    C, _ = run(A, dtype, cutoff)
+    err = oracle.normwise_error(C, oracle.ata_packed(A), n)
+    assert err <= NORM_TOL[dtype], err
+
+
+@pytest.mark.parametrize("dtype", MODES32)
+def test_scaled_columns(gpu, dtype):
+    # config-3 recipe at a small size: every 8th column scaled by 1e3
+    A = inputs.scaled_cols(2048, 1024, seed=2)
+    C, _ = run(A, dtype, 256)
+    err = oracle.normwise_error(C, oracle.ata_packed(A), 1024)
+    assert err <= NORM_TOL[dtype], err
+
+
+@pytest.mark.parametrize("m,n,cutoff", [(1200, 800, 128), (257, 513, 64), (2000, 1000, 256)])
+def test_ozaki_componentwise(gpu, m, n, cutoff):
+    A = inputs.normal(m, n, seed=11)
+    C, _ = run(A, ata.ATA_F64_OZAKI, cutoff)
+    err = oracle.componentwise_error(C, oracle.ata_packed(A), oracle.abs_gram_packed(A))
+    assert err <= 1e-11, err
+
+
+def test_ozaki_wide_exponent_range(gpu):
+    # columns spanning 2^-200 .. 2^200: the per-column scaling keeps each
+    # classical leaf within the componentwise bound.  (Strassen sums mix
+    # columns of different scale, so its error is bounded only normwise;
+    # this case therefore runs the classical products.)
+    rng = np.random.default_rng(5)
+    A = inputs.normal(600, 300, seed=12)
+    A *= np.exp2(rng.integers(-200, 200, size=300))[None, :]
+    C, _ = run(A, ata.ATA_F64_OZAKI, 128, max_strassen_levels=0)
+    err = oracle.componentwise_error(C, oracle.ata_packed(A), oracle.abs_gram_packed(A))
+    assert err <= 1e-11, err
+
+
+def test_tc_batched_equals_single(gpu):
+    import torch
+    shapes = [(300, 200), (1000, 129), (129, 400), (777, 333)]
+    mats = [inputs.normal(m, n, seed=i, dtype=np.float32) for i, (m, n) in enumerate(shapes)]
+    plans = [ata.Plan(m, n, ata.ATA_F32_BF16X3, 128) for m, n in shapes]
+    dev = [torch.from_numpy(a).cuda() for a in mats]
+    singles = [p(d).clone() for p, d in zip(plans, dev)]
+    Cs = ata.ata_execute_batched(plans, dev)
+    torch.cuda.synchronize()
+    for s, c in zip(singles, Cs):
+        assert torch.equal(s, c)
+
+
+def sampled_normwise(A_np, C, n, count, seed):
+    """Normwise error estimated from every diagonal entry plus a uniform
+    sample of off-diagonal entries (weighted up to the full triangle)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    I = rng.integers(0, n, size=count)
+    J = rng.integers(0, n, size=count)
+    keep = I != J
+    I, J = np.minimum(I, J)[keep], np.maximum(I, J)[keep]
+    d = np.arange(n)
+    idx_d = torch.from_numpy(oracle.packed_index(d, d, n)).cuda()
+    idx_o = torch.from_numpy(oracle.packed_index(I, J, n)).cuda()
+    got_d, got_o = C[idx_d].cpu().numpy(), C[idx_o].cpu().numpy()
+    ref_d = oracle.ata_entries(A_np, d, d)
+    ref_o = oracle.ata_entries(A_np, I, J)
+    w = (n * (n - 1) / 2) / I.size * 2.0
+    num = np.sum((got_d - ref_d) ** 2) + w * np.sum((got_o - ref_o) ** 2)
+    den = np.sum(ref_d ** 2) + w * np.sum(ref_o ** 2)
+    return float(np.sqrt(num / den))
+
+
+@pytest.mark.parametrize("dtype", MODES32)
+def test_config3_full_size_sampled(gpu, dtype):
+    """16384 x 8192 FP32, every 8th column x 1e3 (BASELINE config 3), at the
+    bench's cutoff: sampled normwise error within the stated bound."""
+    import torch
+    A_np = inputs.scaled_cols(16384, 8192, seed=2)
+    plan = ata.Plan(16384, 8192, dtype, 0)
+    C = plan(torch.from_numpy(A_np).cuda())
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    err = sampled_normwise(A_np, C, 8192, 20000, seed=3)
+    assert err <= NORM_TOL[dtype], err
+    del C, plan
+    torch.cuda.empty_cache()
+
+
+def test_ozaki_paper_scale_sampled(gpu):
+    import torch
+    from tests.test_gpu_f64 import sample_indices
+    n = 10000
+    A_np = inputs.normal(n, n, seed=1)
+    plan = ata.Plan(n, n, ata.ATA_F64_OZAKI, 0)
+    C = plan(torch.from_numpy(A_np).cuda())
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    I, J = sample_indices(n, 3000, seed=9, cuts=[n // 2, n // 4])
+    got = C[torch.from_numpy(oracle.packed_index(I, J, n)).cuda()].cpu().numpy()
+    err = oracle.componentwise_error(got, oracle.ata_entries(A_np, I, J), oracle.ata_entries(A_np, I, J, absval=True))
+    assert err <= 1e-11, err
+    del C, plan
+    torch.cuda.empty_cache()

@@ -35,20 +35,52 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (m, n, dtype, generator, seed, cutoff)
+    # name: (m, n, leaf mode, generator, seed, cutoff (0 = autotune))
+    # paper scale, FP64 input, 1e-11 componentwise: plain FP64 leaves ...
     "ata_f64_10000x10000": (10000, 10000, "f64", "normal", 1, 0),
     "ata_f64_5000x5000": (5000, 5000, "f64", "normal", 1, 0),
     "ata_f64_20000x8000": (20000, 8000, "f64", "normal", 1, 0),
+    # ... and FP64-accurate leaves emulated on bf16 tensor cores
+    "ata_ozaki_10000x10000": (10000, 10000, "ozaki", "normal", 1, 0),
+    "ata_ozaki_5000x5000": (5000, 5000, "ozaki", "normal", 1, 0),
+    "ata_ozaki_20000x8000": (20000, 8000, "ozaki", "normal", 1, 0),
+    # precision form: FP32 16384 x 8192, every 8th column x 1e3
+    "ata_bf16x3_16384x8192": (16384, 8192, "bf16x3", "scaled_cols", 2, 0),
+    "ata_tf32_16384x8192": (16384, 8192, "tf32", "scaled_cols", 2, 0),
     "ata_f64_512x384": (512, 384, "f64", "uniform", 0, 64),
-    # small case for ncu captures of the leaf kernel (A 162 MB > L2, ~1 GB workspace)
+    # small cases for ncu captures (A larger than L2, a few GB on the device)
     "ata_f64_4500x4500_c600": (4500, 4500, "f64", "normal", 1, 600),
+    "ata_ozaki_4500x4500_c1200": (4500, 4500, "ozaki", "normal", 1, 1200),
+    "ata_bf16x3_8192x4096_c1024": (8192, 4096, "bf16x3", "scaled_cols", 2, 1024),
 }
+MODE_CODES = {"f64": 0, "bf16x3": 1, "tf32": 2, "ozaki": 3}
+PAIRS = {"f64": 1, "bf16x3": 6, "tf32": 1, "ozaki": 21}
+TOLERANCE = {"f64": ("componentwise", 1e-11), "ozaki": ("componentwise", 1e-11),
+             "bf16x3": ("normwise", 1e-6), "tf32": ("normwise", 1e-3)}
 DEFAULT_WORKLOAD = "ata_f64_10000x10000"
 
 # Peak of the FP64 leaf arithmetic: 2 DFMA per clock per SM (the step-0
 # probe measured 1.204 TFLOP/s of DFMA on 152 SMs) at the 2070 MHz maximum
 # SM clock: 152 * 2 * 2 FLOP * 2.07e9 = 1.2586 TFLOP/s.
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Tensor peaks: the measured cuBLAS bf16 burst figure (MEASURED_PEAKS.json
+# bf16_tflops, 1886.9 TFLOP/s when this was written); TF32 is that figure
+# times the nominal tf32/bf16 ratio (1.1 / 2.25).
+BF16_FALLBACK_TFLOPS = 1886.9
+
+
+def tensor_peak(mode):
+    bf16 = BF16_FALLBACK_TFLOPS
+    src = "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+            src = "measured"
+    except Exception:
+        pass
+    if mode == "tf32":
+        return bf16 * 1.1 / 2.25, f"{src} bf16 x nominal tf32/bf16"
+    return bf16, f"{src} bf16 (burst)"
 
 # DRAM traffic of the leaf kernel from one ncu capture, per launch, valid only
 # for the kernel source it was taken on (sha256 of kernels_f64.cu).
@@ -66,9 +98,34 @@ def effective_flops(m, n):
 
 def make_input(name):
     from paper_1902_02104_gb300 import inputs
-    m, n, dt, gen, seed, _ = WORKLOADS[name]
+    m, n, mode, gen, seed, _ = WORKLOADS[name]
     A = getattr(inputs, gen)(m, n, seed=seed)
-    return A.astype(np.float64 if dt == "f64" else np.float32)
+    return A.astype(np.float64 if mode in ("f64", "ozaki") else np.float32)
+
+
+def sampled_error(oracle, A_np, C, n, kind, dev, torch, count=2000, seed=123):
+    """Componentwise error over sampled entries, or the normwise error
+    estimated from every diagonal entry plus sampled off-diagonal ones."""
+    rng = np.random.default_rng(seed)
+    I = rng.integers(0, n, size=count)
+    J = rng.integers(0, n, size=count)
+    I, J = np.minimum(I, J), np.maximum(I, J)
+    if kind == "componentwise":
+        got = C[torch.from_numpy(oracle.packed_index(I, J, n)).to(dev)].cpu().numpy()
+        ref = oracle.ata_entries(A_np, I, J)
+        G = oracle.ata_entries(A_np, I, J, absval=True)
+        return oracle.componentwise_error(got, ref, G)
+    keep = I != J
+    I, J = I[keep], J[keep]
+    d = np.arange(n)
+    got_d = C[torch.from_numpy(oracle.packed_index(d, d, n)).to(dev)].cpu().numpy()
+    got_o = C[torch.from_numpy(oracle.packed_index(I, J, n)).to(dev)].cpu().numpy()
+    ref_d = oracle.ata_entries(A_np, d, d)
+    ref_o = oracle.ata_entries(A_np, I, J)
+    w = (n * (n - 1) / 2) / max(I.size, 1) * 2.0
+    num = np.sum((got_d - ref_d) ** 2) + w * np.sum((got_o - ref_o) ** 2)
+    den = np.sum(ref_d ** 2) + w * np.sum(ref_o ** 2)
+    return float(np.sqrt(num / den))
 
 
 class ClockSampler:
@@ -188,7 +245,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     name = args.workload
-    m, n, dt, gen, seed, cutoff = WORKLOADS[name]
+    m, n, mode, gen, seed, cutoff = WORKLOADS[name]
     A = make_input(name)
     eff = effective_flops(m, n)
     # each step: a bounded sample (~budget seconds) of the oracle
@@ -234,10 +291,11 @@ def run_ours(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     name = args.workload
-    m, n, dt, gen, seed, cutoff = WORKLOADS[name]
+    m, n, mode, gen, seed, cutoff = WORKLOADS[name]
+    if args.cutoff is not None:
+        cutoff = args.cutoff
     A_np = make_input(name)
-    dtype = ata.ATA_F64 if dt == "f64" else ata.ATA_F32_BF16X3
-    plan = ata.Plan(m, n, dtype, cutoff)
+    plan = ata.Plan(m, n, MODE_CODES[mode], cutoff)
     info = plan.info
     A = torch.from_numpy(A_np).to(dev)
     C = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
@@ -255,7 +313,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    leaf_ms, split_ms, comb_ms = [], [], []
+    leaf_ms, split_ms, comb_ms, prep_ms = [], [], [], []
     e0.record(stream)
     for _ in range(args.steps):
         plan(A, C)
@@ -263,6 +321,7 @@ def run_ours(args):
         st = plan.stage_times()
         leaf_ms.append(st["leaf_ms"])
         split_ms.append(st["split_ms"])
+        prep_ms.append(st["prep_ms"])
         comb_ms.append(st["combine_ms"])
     e1.record(stream)
     torch.cuda.synchronize()
@@ -272,16 +331,10 @@ def run_ours(args):
     ms_max = max_over_ranks(torch, ms, world)
 
     # accuracy at the stated tolerance: sampled entries against the oracle
-    rng = np.random.default_rng(123)
+    err_kind, tol = TOLERANCE[mode]
     cnt = 2000
-    I = rng.integers(0, n, size=cnt)
-    J = rng.integers(0, n, size=cnt)
-    I, J = np.minimum(I, J), np.maximum(I, J)
-    idx = torch.from_numpy(oracle.packed_index(I, J, n)).to(dev)
-    got = C[idx].cpu().numpy()
-    ref = oracle.ata_entries(A_np, I, J)
-    G = oracle.ata_entries(A_np, I, J, absval=True)
-    err_c = oracle.componentwise_error(got, ref, G)
+    err = sampled_error(oracle, A_np, C, n, err_kind, dev, torch, count=cnt)
+    dev_status = plan.device_status()
 
     # end to end through the C ABI from pinned host memory
     A_host = torch.from_numpy(A_np).pin_memory()
@@ -298,22 +351,32 @@ def run_ours(args):
     eff = effective_flops(m, n)
     value = world * eff / (ms_max / 1e3) / 1e12
     leaf_s = statistics.mean(leaf_ms) / 1e3
-    achieved = 2.0 * info["mults"] / leaf_s / 1e12
-    sha = _src_sha(os.path.join(ROOT, "paper_1902_02104_gb300", "csrc", "kernels_f64.cu"))
+    leaf_flops = 2.0 * info["mults"] * PAIRS[mode]
+    achieved = leaf_flops / leaf_s / 1e12
+    if mode == "f64":
+        kern, src, bound, peak, peak_src = "leaf_f64_kernel", "kernels_f64.cu", "alu", FP64_ALU_PEAK_TFLOPS, \
+            "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"
+    else:
+        kern, src, bound = "tc_gemm_kernel", "leaf_tc.cu", "tensor"
+        peak, peak_src = tensor_peak(mode)
+    sha = _src_sha(os.path.join(ROOT, "paper_1902_02104_gb300", "csrc", src))
     tr = LEAF_TRAFFIC.get((name, sha))
     line = {
         "metric": "effective TFLOP/s (m*n^2 FMAs) of C = A^t A", "value": value, "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
-        "config": {"workload": name, "m": m, "n": n, "generator": f"{gen}(seed={seed})", "cutoff": info["cutoff"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "ozaki": "bf16 (FP64 emulation, 6 slices)", "bf16x3": "bf16 (3 slices)",
+                  "tf32": "tf32"}[mode], "data": "synthetic",
+        "config": {"workload": name, "m": m, "n": n, "leaf": mode, "generator": f"{gen}(seed={seed})",
+                   "cutoff": info["cutoff"],
                    "strassen_levels_max": info["max_strassen_levels"], "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (A is %d MB)" % (A_np.nbytes >> 20)},
-        "error": {"componentwise_sampled": err_c, "tolerance": 1e-11, "samples": cnt},
-        "stages_ms": {"split": statistics.mean(split_ms), "leaf": statistics.mean(leaf_ms),
-                      "combine": statistics.mean(comb_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": tr,
-                     "kernel": "leaf_f64_kernel", "flops_per_launch": 2.0 * info["mults"]},
+        "error": {err_kind + "_sampled": err, "tolerance": tol, "samples": cnt, "device_status": dev_status},
+        "stages_ms": {"split": statistics.mean(split_ms), "prep": statistics.mean(prep_ms),
+                      "leaf": statistics.mean(leaf_ms), "combine": statistics.mean(comb_ms)},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
+                     "kernel": kern, "flops_per_launch": leaf_flops},
         "e2e": {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_np.nbytes),
                 "d2h_bytes_per_step": int(C.numel() * 8)},
         "gpu_launches": int(args.steps * info["n_launches"]),
@@ -342,6 +405,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cutoff", type=int, default=None, help="override the workload's cutoff")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

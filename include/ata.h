@@ -185,16 +185,15 @@ ata_status ata_execute_batched(const ata_plan* plans, int count,
                                double* const* C_packed, void* stream);
 
 /* Stage timing.  With enable != 0 the plan's graph also records CUDA events
- * on the execution stream before the operand-split launches, before and
- * after the leaf launch, and after the combine launches (the graph is
- * re-captured on the next ata_execute).  ata_plan_stage_times returns, for
- * the most recent execution (which must have completed), the milliseconds
- * of the split launches, the leaf launch and the combine launches.
+ * on the execution stream around its stages (the graph is re-captured on the
+ * next ata_execute).  ata_plan_stage_times fills ms[4] for the most recent
+ * execution (which must have completed): the Strassen operand-split
+ * launches, the leaf operand preparation (tensor-core modes; 0 for FP64),
+ * the leaf product kernel, and the Strassen combine launches.
  * Errors: ATA_EINVAL (NULL arguments, timing not enabled, no execution yet),
  * ATA_ECUDA. */
 ata_status ata_plan_enable_stage_timing(ata_plan plan, int enable);
-ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms,
-                                float* combine_ms);
+ata_status ata_plan_stage_times(ata_plan plan, float* ms);
 
 /* Error word of the plan's tensor-core kernels (0 = none).  Their waits on
  * pipeline barriers are bounded (1 s); a wait that gives up records a

@@ -88,8 +88,7 @@ def load():
         "ata_execute_static_scratch": ([i64, i64, vp, i64, dp, i32, vp], i32),
         "ata_plan_device_status": ([vp, ctypes.POINTER(ctypes.c_int)], i32),
         "ata_plan_enable_stage_timing": ([vp, i32], i32),
-        "ata_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
-                                  ctypes.POINTER(ctypes.c_float)], i32),
+        "ata_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_float)], i32),
         "ata_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i32, i32], i32),
         "ata_submit": ([vp, i64, i64, vp, i64, dp, ctypes.POINTER(ctypes.c_uint64)], i32),
         "ata_poll": ([vp, ctypes.c_uint64, i32], i32),
@@ -172,11 +171,11 @@ class Plan:
         _check(load().ata_plan_enable_stage_timing(self.handle, int(enable)))
 
     def stage_times(self) -> dict:
-        """Milliseconds of the split, leaf and combine stages of the last
-        (completed) execution; needs enable_stage_timing()."""
-        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
-        _check(load().ata_plan_stage_times(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return {"split_ms": a.value, "leaf_ms": b.value, "combine_ms": c.value}
+        """Milliseconds of the split, prep, leaf and combine stages of the
+        last (completed) execution; needs enable_stage_timing()."""
+        ms = (ctypes.c_float * 4)()
+        _check(load().ata_plan_stage_times(self.handle, ms))
+        return {"split_ms": ms[0], "prep_ms": ms[1], "leaf_ms": ms[2], "combine_ms": ms[3]}
 
     def __call__(self, A, C=None, stream=None):
         return ata_execute(self, A, C, stream)

@@ -805,7 +805,7 @@ bool encode_for(LeafKind k, CUtensorMap* map, char* base, int rows_pad, int K_pa
 int g_sms = 1;  // SM count of the device (set before any capture)
 
 template <int NB, int MODE>
-cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s) {
+cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s, cudaEvent_t before_gemm) {
     if (Geo<MODE>::SLICED) {
         cudaError_t e = cudaMemsetAsync(t.tc_ex, 0, t.tc_ex_bytes, s);
         if (e != cudaSuccess) return e;
@@ -813,17 +813,21 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
             tc_colmax_kernel<NB, typename PrepSrc<MODE>::T><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
     }
     if (t.nprep > 0) tc_prep_kernel<NB, MODE><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
+    if (before_gemm) {
+        cudaError_t e = cudaEventRecordWithFlags(before_gemm, s, cudaEventRecordExternal);
+        if (e != cudaSuccess) return e;
+    }
     const int grid = std::max(1, std::min(t.ntiles, g_sms));
     tc_gemm_kernel<NB, MODE><<<grid, threads_of<MODE>(), smem_bytes<MODE>(), s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status);
     return cudaGetLastError();
 }
 
 template <int NB>
-cudaError_t launch_kind(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s) {
+cudaError_t launch_kind(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s, cudaEvent_t ev) {
     switch (t.leaf) {
-        case LEAF_BF16X3: return launch_mode<NB, MODE_BF16X3>(t, bs, s);
-        case LEAF_TF32: return launch_mode<NB, MODE_TF32>(t, bs, s);
-        case LEAF_OZAKI: return launch_mode<NB, MODE_OZAKI>(t, bs, s);
+        case LEAF_BF16X3: return launch_mode<NB, MODE_BF16X3>(t, bs, s, ev);
+        case LEAF_TF32: return launch_mode<NB, MODE_TF32>(t, bs, s, ev);
+        case LEAF_OZAKI: return launch_mode<NB, MODE_OZAKI>(t, bs, s, ev);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -940,16 +944,16 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     return ATA_OK;
 }
 
-ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s) {
+ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s, cudaEvent_t before_gemm) {
     cudaError_t e;
     if (nb <= 1) {
         BindSet<1> bs{};
         bs.b[0] = binds[0];
-        e = launch_kind<1>(t, bs, s);
+        e = launch_kind<1>(t, bs, s, before_gemm);
     } else if (nb <= kMaxBatchBind) {
         BindSet<kMaxBatchBind> bs{};
         for (int i = 0; i < nb; ++i) bs.b[i] = binds[i];
-        e = launch_kind<kMaxBatchBind>(t, bs, s);
+        e = launch_kind<kMaxBatchBind>(t, bs, s, before_gemm);
     } else {
         return fail(ATA_EINVAL, "too many instances in one launch");
     }

@@ -234,19 +234,21 @@ ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cuda
     if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
     if (t.ntiles > 0) {
         if (t.leaf == LEAF_F64) {
+            if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
             const int grid = std::max(1, std::min(t.ntiles, sms * per_sm));
             ATA_CUDA(launch_leaf_f64(binds, nb, t.prods, t.terms, t.tiles, t.ntiles, t.counter, grid, s));
         } else {
-            ata_status st = launch_leaf_tc(t, binds, nb, s);
+            ata_status st = launch_leaf_tc(t, binds, nb, s, ev ? ev[2] : nullptr);
             if (st != ATA_OK) return st;
         }
     }
-    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
+    if (ev && t.ntiles == 0) ATA_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
+    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     for (int l = (int)t.comb_lv.size() - 1; l >= 0; --l) {
         const LevelRange& lr = t.comb_lv[l];
         ATA_CUDA(launch_combine(binds, nb, t.comb, t.comb_chunks + lr.chunk0, lr.nchunks, s));
     }
-    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
+    if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal));
     return ATA_OK;
 }
 
@@ -254,7 +256,7 @@ ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cuda
 ata_status capture_graph(const DeviceTables& t, const Bind* binds, int nb, GraphCache* g) {
     if (!g->cap_stream) ATA_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     if (g->timing && !g->ev[0])
-        for (int i = 0; i < 4; ++i) ATA_CUDA(cudaEventCreate(&g->ev[i]));
+        for (int i = 0; i < 5; ++i) ATA_CUDA(cudaEventCreate(&g->ev[i]));
     {
         int sms, per_sm;
         device_params(&sms, &per_sm);  // before capture: attribute queries are not captured work
@@ -290,9 +292,9 @@ ata_status capture_graph(const DeviceTables& t, const Bind* binds, int nb, Graph
 void GraphCache::release() {
     if (exec) cudaGraphExecDestroy(exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
-    for (int i = 0; i < 4; ++i) ev[i] = nullptr;
+    for (int i = 0; i < 5; ++i) ev[i] = nullptr;
     exec = nullptr;
     cap_stream = nullptr;
     binds.clear();
@@ -608,14 +610,12 @@ ata_status ata_plan_enable_stage_timing(ata_plan plan, int enable) {
     return ATA_OK;
 }
 
-ata_status ata_plan_stage_times(ata_plan plan, float* split_ms, float* leaf_ms, float* combine_ms) {
-    if (!plan || !split_ms || !leaf_ms || !combine_ms) return fail(ATA_EINVAL, "NULL argument");
+ata_status ata_plan_stage_times(ata_plan plan, float* ms) {
+    if (!plan || !ms) return fail(ATA_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(plan->mu);
     if (!plan->graph.timing || !plan->graph.timed_run || !plan->graph.ev[0])
         return fail(ATA_EINVAL, "stage timing is not enabled or nothing has run");
-    ATA_CUDA(cudaEventElapsedTime(split_ms, plan->graph.ev[0], plan->graph.ev[1]));
-    ATA_CUDA(cudaEventElapsedTime(leaf_ms, plan->graph.ev[1], plan->graph.ev[2]));
-    ATA_CUDA(cudaEventElapsedTime(combine_ms, plan->graph.ev[2], plan->graph.ev[3]));
+    for (int i = 0; i < 4; ++i) ATA_CUDA(cudaEventElapsedTime(&ms[i], plan->graph.ev[i], plan->graph.ev[i + 1]));
     return ATA_OK;
 }
 

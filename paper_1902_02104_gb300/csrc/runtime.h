@@ -90,7 +90,7 @@ struct GraphCache {
     std::vector<Bind> binds;
     bool timing = false;        // graph records ev[] around its stages
     bool timed_run = false;     // an execution with timing has been queued
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     void release();
 };
 
@@ -106,7 +106,8 @@ ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cuda
 ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, GraphCache* g, cudaStream_t s);
 
 // Tensor-core leaf launch (bf16x3 / TF32 / FP64 emulation).
-ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s);
+ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s,
+                          cudaEvent_t before_gemm = nullptr);
 ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d);
 bool leaf_supported(LeafKind k);
 int leaf_tile(LeafKind k);

@@ -136,7 +136,7 @@ def test_stage_timing(gpu):
     plan(A)
     torch.cuda.synchronize()
     t = plan.stage_times()
-    assert t["leaf_ms"] > 0 and t["split_ms"] >= 0 and t["combine_ms"] >= 0
+    assert t["leaf_ms"] > 0 and t["split_ms"] >= 0 and t["combine_ms"] >= 0 and t["prep_ms"] >= 0
 
 
 def sample_indices(n, count, seed, cuts=()):

@@ -188,10 +188,12 @@ __device__ __forceinline__ long long f2d_bits(float f) {
 }
 
 // Scale exponent E of a column whose largest magnitude has bit pattern mx:
-// mx = f * 2^E with f in [0.5, 1); 0 for an all-zero (or subnormal) column.
+// mx = f * 2^E with f in [0.5, 1); 0 for an all-zero (or subnormal) column;
+// kNonFinite when the column holds an Inf or NaN (its products become NaN).
+constexpr int kNonFinite = 1 << 20;
 __device__ __forceinline__ int col_exponent(unsigned long long mx) {
     const int eb = (int)((mx >> 52) & 0x7FF);
-    return eb == 0 ? 0 : eb - 1022;
+    return eb == 0 ? 0 : eb == 0x7FF ? kNonFinite : eb - 1022;
 }
 
 // K-major shared-memory matrix descriptor (tcgen05 "matrix descriptor"):
@@ -232,31 +234,35 @@ __device__ __forceinline__ int64_t packed_start(int64_t i, int64_t n) { return i
 //            drained after the chunk's last K-block;
 //   F group: the other orders (FMIN..FMAX) in one accumulator, either over
 //            the whole K (F_FINAL) or drained per chunk like the D group.
-// The float-float running sums (hi, lo) of a thread's columns: hi always in
-// registers, lo in TMEM (LO_TMEM) or in registers.
+// The float-float running sums (hi, lo) of a thread's columns: hi in
+// registers, lo in shared memory.
 
 template <int MODE>
 struct Geo;
 
+// D group: orders 0..DMAX, order d into accumulator min(d, ND - 1), drained
+// after every chunk of KC; accumulator 0 holds order 0 alone and is exact.
+// DBUF > 1 double-buffers the D group.  F group: orders FMIN..FMAX in one
+// accumulator, over the whole K (F_FINAL) or drained per chunk.
 template <>
 struct Geo<MODE_BF16X3> {
-    static constexpr int PARTS = 3, ELEM = 2, KBLK = 64, ROWB = 128, KSTEP = 16, NSTAGE = 2;
-    static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
-    static constexpr int KC = 128, ND = 2, FMIN = 2, FMAX = 2;
-    static constexpr bool F_FINAL = true, LO_TMEM = true, LO_SMEM = false, SLICED = true;
-    static constexpr int EPI_WARPS = 8;
-    static constexpr uint32_t TMEM_COLS = 512, F_COL = 256, LO_COL = 384;
+    static constexpr int PARTS = 3, ELEM = 2, KBLK = 32, ROWB = 64, KSTEP = 16, NSTAGE = 3;
+    static constexpr uint32_t SWZ = 4, SBO = 512;  // 64B swizzle
+    static constexpr int KC = 256, ND = 2, DMAX = 2, DBUF = 2, FMIN = 1, FMAX = 0;  // no F group
+    static constexpr bool F_FINAL = false, SLICED = true;
+    static constexpr int EPI_WARPS = 16;
+    static constexpr uint32_t TMEM_COLS = 512, F_COL = 0;
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 };
 
 template <>
 struct Geo<MODE_TF32> {
     static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6;
-    static constexpr uint32_t SWZ = 2, SBO = 1024;
-    static constexpr int KC = 1 << 30, ND = 0, FMIN = 0, FMAX = 0;
-    static constexpr bool F_FINAL = true, LO_TMEM = false, LO_SMEM = false, SLICED = false;
+    static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
+    static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0;
+    static constexpr bool F_FINAL = true, SLICED = false;
     static constexpr int EPI_WARPS = 8;
-    static constexpr uint32_t TMEM_COLS = 128, F_COL = 0, LO_COL = 0;
+    static constexpr uint32_t TMEM_COLS = 128, F_COL = 0;
     static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 };
 
@@ -264,10 +270,10 @@ template <>
 struct Geo<MODE_OZAKI> {
     static constexpr int PARTS = 6, ELEM = 2, KBLK = 16, ROWB = 32, KSTEP = 16, NSTAGE = 3;
     static constexpr uint32_t SWZ = 6, SBO = 256;  // 32B swizzle
-    static constexpr int KC = 128, ND = 3, FMIN = 3, FMAX = 5;
-    static constexpr bool F_FINAL = false, LO_TMEM = false, LO_SMEM = true, SLICED = true;
+    static constexpr int KC = 128, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5;
+    static constexpr bool F_FINAL = false, SLICED = true;
     static constexpr int EPI_WARPS = 16;
-    static constexpr uint32_t TMEM_COLS = 512, F_COL = 384, LO_COL = 0;
+    static constexpr uint32_t TMEM_COLS = 512, F_COL = 384;
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 };
 
@@ -281,7 +287,7 @@ __host__ __device__ constexpr int stage_bytes() {
 }
 template <int MODE>
 __host__ __device__ constexpr int lo_smem_bytes() {
-    return Geo<MODE>::LO_SMEM ? 128 * 128 * 4 : 0;
+    return Geo<MODE>::ND > 0 ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
 }
 template <int MODE>
 __host__ __device__ constexpr int smem_bytes() {
@@ -297,6 +303,14 @@ __host__ __device__ constexpr int threads_of() {
 
 template <typename TS, int NB>
 __device__ __forceinline__ TS operand_value(const BindSet<NB>& bs, const Term* ts, int t0, int nt, int k, int c) {
+    if (nt == 1) {  // one term: no floating-point addition (sign applied to the bits)
+        const Term& tm = ts[t0];
+        if (k >= tm.rows || c >= tm.cols) return TS(0);
+        const Bind& b = bs.b[tm.inst];
+        const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
+        const TS x = __ldg(base + tm.off + (int64_t)k * tm.ld + c);
+        return tm.neg ? -x : x;
+    }
     TS v = 0;
     for (int t = 0; t < nt; ++t) {
         const Term& tm = ts[t0 + t];
@@ -348,7 +362,7 @@ __device__ __forceinline__ void slice_digits(double x, int E, int (&d)[S]) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
     long long v = 0;
-    if (eb != 0 && eb != 0x7FF) {
+    if (eb != 0 && eb != 0x7FF && E < kNonFinite) {
         const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
         const int shift = (eb - 1075) + 8 * S - E;
         if (shift >= 0)
@@ -364,6 +378,29 @@ __device__ __forceinline__ void slice_digits(double x, int E, int (&d)[S]) {
         v = (v - r) >> 8;
     }
     d[0] = (int)v;
+}
+
+// The same for an FP32 value and S = 3 (24 bits) in 32-bit integers.
+__device__ __forceinline__ void slice_digits(float x, int E, int (&d)[3]) {
+    const unsigned int bits = __float_as_uint(x);
+    const int eb = (int)((bits >> 23) & 0xFF);
+    int v = 0;
+    if (eb != 0 && eb != 0xFF && E < kNonFinite) {
+        const int m = (int)((bits & 0x7FFFFF) | 0x800000);
+        const int shift = (eb - 150) + 24 - E;
+        if (shift >= 0)
+            v = m << shift;
+        else if (shift > -31)
+            v = (int)(((long long)m + (1LL << (-shift - 1))) >> (-shift));
+        if (bits >> 31) v = -v;
+    }
+#pragma unroll
+    for (int s = 2; s >= 1; --s) {
+        const int r = ((v + 128) & 255) - 128;
+        d[s] = r;
+        v = (v - r) >> 8;
+    }
+    d[0] = v;
 }
 
 template <int MODE>
@@ -421,16 +458,16 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
         const unsigned long long mx =
             reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
         const int E = col_exponent(mx);
+        int dg[8][S];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) slice_digits(tile[kc * 8 + i][col], E, dg[i]);
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
+            const float unit = __int_as_float((127 - 8 * (s + 1)) << 23);  // 2^-8(s+1)
             __nv_bfloat16 q[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                int d[S];
-                slice_digits<S>((double)tile[kc * 8 + i][col], E, d);
-                q[i] = __float2bfloat16_rn(__int2float_rn(d[s]) * __int_as_float((127 - 8 * (s + 1)) << 23));
-            }
+            for (int i = 0; i < 8; ++i) q[i] = __float2bfloat16_rn(__int2float_rn(dg[i][s]) * unit);
             *reinterpret_cast<uint4*>(out + s * part_elems + base) = *reinterpret_cast<const uint4*>(q);
         }
     }
@@ -448,16 +485,17 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
     constexpr int NCOL = 128 / (G::EPI_WARPS / 4);  // columns per epilogue thread
     constexpr int NG = NCOL / 16;                   // 16-column groups per thread
     constexpr int kbpc = G::KC / G::KBLK > 0 ? G::KC / G::KBLK : 1;
-    constexpr bool HAS_F = true;
+    constexpr bool HAS_F = G::FMIN <= G::FMAX;
+    constexpr int NKS = G::KBLK / G::KSTEP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* lo_s = reinterpret_cast<float*>(smem + G::NSTAGE * stage_bytes<MODE>());  // [col][row] (LO_SMEM)
+    float* lo_s = reinterpret_cast<float*>(smem + G::NSTAGE * stage_bytes<MODE>());  // [col][row]
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * stage_bytes<MODE>() + lo_smem_bytes<MODE>());
-    // barriers: full[NSTAGE] empty[NSTAGE] dfull dempty ffull fempty done ; tmem slot
+    // barriers: full[NSTAGE] empty[NSTAGE] dfull[DBUF] dempty[DBUF] ffull fempty done ; tmem slot
     const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * G::NSTAGE;
-    const uint32_t b_dfull = b_empty + 8 * G::NSTAGE, b_dempty = b_dfull + 8;
-    const uint32_t b_ffull = b_dempty + 8, b_fempty = b_ffull + 8, b_done = b_fempty + 8;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * G::NSTAGE + 5);
+    const uint32_t b_dfull = b_empty + 8 * G::NSTAGE, b_dempty = b_dfull + 8 * G::DBUF;
+    const uint32_t b_ffull = b_dempty + 8 * G::DBUF, b_fempty = b_ffull + 8, b_done = b_fempty + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * G::NSTAGE + 2 * G::DBUF + 3);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -465,8 +503,10 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
             mbar_init(b_full + 8 * s, 1);
             mbar_init(b_empty + 8 * s, 1);
         }
-        mbar_init(b_dfull, 1);
-        mbar_init(b_dempty, G::EPI_WARPS);
+        for (int s = 0; s < G::DBUF; ++s) {
+            mbar_init(b_dfull + 8 * s, 1);
+            mbar_init(b_dempty + 8 * s, G::EPI_WARPS);
+        }
         mbar_init(b_ffull, 1);
         mbar_init(b_fempty, G::EPI_WARPS);
         mbar_init(b_done, 1);
@@ -524,7 +564,6 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
         if (lane == 0) {
             uint32_t it = 0, chunk = 0, tcount = 0;
             bool ok = true;
-            constexpr int NKS = G::KBLK / G::KSTEP;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
                 const LeafTile lt = tiles[t];
                 const int nkb = tcp[lt.prod].K_pad / G::KBLK;
@@ -537,9 +576,9 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const bool first_in_chunk = (kb % kbpc) == 0;
                     const bool last_in_chunk = (kb % kbpc) == kbpc - 1 || kb == nkb - 1;
-                    const uint32_t cpar = ((chunk & 1) ^ 1);
+                    const uint32_t buf = chunk % G::DBUF;
                     if (G::ND > 0 && first_in_chunk) {
-                        if (!mbar_wait(b_dempty, cpar, status, ERR_TIMEOUT_MMA)) {
+                        if (!mbar_wait(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
                             ok = false;
                             break;
                         }
@@ -558,28 +597,33 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                         return make_desc(st + (G::PARTS + q) * tile_bytes<MODE>() + ks * G::KSTEP * G::ELEM, G::SBO,
                                          G::SWZ);
                     };
-                    // D group: order d into accumulator d, overwritten at the chunk's start
+                    if constexpr (G::ND > 0) {
+                        // D group: order d into accumulator min(d, ND-1); each accumulator is
+                        // overwritten by its first MMA of the chunk
+                        bool fresh[3] = {first_in_chunk, first_in_chunk, first_in_chunk};
 #pragma unroll
-                    for (int ord = 0; ord < G::ND; ++ord) {
-                        bool first = first_in_chunk;
+                        for (int ord = 0; ord <= G::DMAX; ++ord) {
+                            const int acc = ord < G::ND - 1 ? ord : G::ND - 1;
+                            const uint32_t d = tmem + (buf * G::ND + acc) * 128;
 #pragma unroll
-                        for (int a = 0; a <= ord; ++a)
+                            for (int a = 0; a <= ord; ++a) {
+                                if (a >= G::PARTS || ord - a >= G::PARTS) continue;
 #pragma unroll
-                            for (int ks = 0; ks < NKS; ++ks) {
-                                umma<MODE>(tmem + ord * 128, desc_a(a, ks), desc_b(ord - a, ks), G::IDESC,
-                                           first ? 0u : 1u);
-                                first = false;
+                                for (int ks = 0; ks < NKS; ++ks) {
+                                    umma<MODE>(d, desc_a(a, ks), desc_b(ord - a, ks), G::IDESC, fresh[acc] ? 0u : 1u);
+                                    fresh[acc] = false;
+                                }
                             }
-                    }
-                    if (G::ND > 0 && last_in_chunk) umma_commit(b_dfull);
-                    // F group
-                    if constexpr (!G::F_FINAL) {
-                        if (first_in_chunk && !mbar_wait(b_fempty, cpar, status, ERR_TIMEOUT_MMA)) {
-                            ok = false;
-                            break;
                         }
+                        if (last_in_chunk) umma_commit(b_dfull + 8 * buf);
                     }
-                    {
+                    if constexpr (HAS_F) {
+                        if (!G::F_FINAL && first_in_chunk) {
+                            if (!mbar_wait(b_fempty, (chunk & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
+                                ok = false;
+                                break;
+                            }
+                        }
                         bool first = G::F_FINAL ? (kb == 0) : first_in_chunk;
 #pragma unroll
                         for (int ord = G::FMIN; ord <= G::FMAX; ++ord)
@@ -593,8 +637,8 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                                     first = false;
                                 }
                             }
+                        if (!G::F_FINAL && last_in_chunk) umma_commit(b_ffull);
                     }
-                    if (!G::F_FINAL && last_in_chunk) umma_commit(b_ffull);
                     umma_commit(b_empty + 8 * s);  // stage reusable once these MMAs finish
                     if (last_in_chunk) ++chunk;
                 }
@@ -609,11 +653,13 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        // Thread = one row (TMEM lane) of the tile and NCOL of its columns.
+        // Thread = one row (TMEM lane) of the tile and NCOL of its columns; the
+        // running sum of the drained chunks is hi (registers) + lo (smem).
         const int e = warp - 2;
         const int q = warp & 3;              // TMEM lane quarter of this warp
         const int cq = e >> 2;               // column slice
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const int row = 32 * q + lane;
         uint32_t chunk = 0, tcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
@@ -624,55 +670,60 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
             float hi[NCOL];
 #pragma unroll
             for (int c = 0; c < NCOL; ++c) hi[c] = 0.f;
-            const int row = 32 * q + lane;
-            // drains one accumulator (TMEM column base) into (hi, lo)
-            auto drain = [&](uint32_t acc_col, bool first_chunk) {
-#pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    float v[16];
-                    tmem_ld16(tmem + lane_base + acc_col + cq * NCOL + g * 16, v);
-                    if constexpr (G::LO_TMEM) {
-                        const uint32_t lo_addr = tmem + lane_base + G::LO_COL + cq * NCOL + g * 16;
-                        float lo[16];
-                        if (first_chunk) {
-#pragma unroll
-                            for (int c = 0; c < 16; ++c) lo[c] = 0.f;
-                        } else {
-                            tmem_ld16(lo_addr, lo);
-                        }
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) ff_add(hi[g * 16 + c], lo[c], v[c]);
-                        tmem_st16(lo_addr, lo);
-                    } else if constexpr (G::LO_SMEM) {
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            float* lp = lo_s + (cq * NCOL + g * 16 + c) * 128 + row;
-                            float lo = first_chunk ? 0.f : *lp;
-                            ff_add(hi[g * 16 + c], lo, v[c]);
-                            *lp = lo;
-                        }
-                    }
-                }
-            };
             if constexpr (G::ND > 0) {
                 for (int ci = 0; ci < nchunks; ++ci, ++chunk) {
-                    if (!mbar_wait(b_dfull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                    const uint32_t buf = chunk % G::DBUF;
+                    if (!mbar_wait(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int acc = 0; acc < G::ND; ++acc) drain(acc * 128, ci == 0 && acc == 0);
+                    for (int g = 0; g < NG; ++g) {
+                        const uint32_t col = cq * NCOL + g * 16;
+                        float a0[16], a1[16];
+                        tmem_ld16(tmem + lane_base + (buf * G::ND + 0) * 128 + col, a0);
+                        tmem_ld16(tmem + lane_base + (buf * G::ND + 1) * 128 + col, a1);
+                        float a2[16];
+                        if constexpr (G::ND > 2) {
+                            tmem_ld16(tmem + lane_base + (buf * G::ND + 2) * 128 + col, a2);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) a2[c] = 0.f;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            // chunk value h + l (accumulator 0 is exact, the others are at
+                            // most ~2^-8 of it), added to (hi, lo) as a float-float sum and
+                            // renormalised so that |lo| stays within half an ulp of hi
+                            float h, l, s2, e2;
+                            two_sum(a0[c], a1[c], h, l);
+                            l += a2[c];
+                            float* lp = lo_s + (col + c) * 128 + row;
+                            two_sum(hi[g * 16 + c], h, s2, e2);
+                            e2 += (ci == 0 ? 0.f : *lp) + l;
+                            const float hn = s2 + e2;       // Fast2Sum: |s2| >= |e2|
+                            *lp = e2 - (hn - s2);
+                            hi[g * 16 + c] = hn;
+                        }
+                    }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(b_dempty);
-                    if constexpr (!G::F_FINAL) {
+                    if (lane == 0) mbar_arrive(b_dempty + 8 * buf);
+                    if constexpr (HAS_F && !G::F_FINAL) {
                         if (!mbar_wait(b_ffull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        drain(G::F_COL, false);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) {
+                            const uint32_t col = cq * NCOL + g * 16;
+                            float f[16];
+                            tmem_ld16(tmem + lane_base + G::F_COL + col, f);
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) lo_s[(col + c) * 128 + row] += f[c];
+                        }
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(b_fempty);
@@ -689,7 +740,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
             }
             // FP64 tile: row i of this thread, NCOL columns in groups of 16
             const Bind& bind = bs.b[pr->inst];
-            const int i = lt.ti * 128 + 32 * q + lane;
+            const int i = lt.ti * 128 + row;
             const int j0 = lt.tj * 128 + cq * NCOL;
             const bool row_ok = i < pr->out_rows;
             int Ei = 0;
@@ -701,18 +752,10 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
             double* prow = bind.C + (packed_start(gi, bind.n) - gi + pr->cj0);
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                float lo[16], f[16];
-                if constexpr (G::LO_TMEM) {
-                    tmem_ld16(tmem + lane_base + G::LO_COL + cq * NCOL + g * 16, lo);
-                } else if constexpr (G::LO_SMEM) {
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) lo[c] = lo_s[(cq * NCOL + g * 16 + c) * 128 + row];
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) lo[c] = 0.f;
-                }
+                const uint32_t col = cq * NCOL + g * 16;
+                float f[16];
                 if constexpr (G::F_FINAL) {
-                    tmem_ld16(tmem + lane_base + G::F_COL + cq * NCOL + g * 16, f);
+                    tmem_ld16(tmem + lane_base + G::F_COL + col, f);
                 } else {
 #pragma unroll
                     for (int c = 0; c < 16; ++c) f[c] = 0.f;
@@ -722,15 +765,19 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                     for (int c = 0; c < 16; ++c) {
                         const int j = j0 + g * 16 + c;
                         if (j < pr->out_cols) {
-                            float hh = hi[g * 16 + c], ll = lo[c];
+                            float hh = hi[g * 16 + c], ll = G::ND > 0 ? lo_s[(col + c) * 128 + row] : 0.f;
                             ff_add(hh, ll, f[c]);
                             long long bh = f2d_bits(hh), bl = f2d_bits(ll);
+                            double v;
                             if constexpr (G::SLICED) {
                                 const int sc = Ei + col_exponent(reinterpret_cast<const unsigned long long*>(pr->ey)[j]);
                                 if (bh) bh += (long long)sc << 52;
                                 if (bl) bl += (long long)sc << 52;
+                                v = sc >= kNonFinite ? __longlong_as_double(0x7FF8000000000000LL)
+                                                     : __longlong_as_double(bh) + __longlong_as_double(bl);
+                            } else {
+                                v = __longlong_as_double(bh) + __longlong_as_double(bl);
                             }
-                            const double v = __longlong_as_double(bh) + __longlong_as_double(bl);
                             if (pr->out_kind == OUT_DENSE) {
                                 dense[j] = v;
                             } else if (pr->out_kind == OUT_PACKED || (int64_t)pr->cj0 + j >= gi) {
@@ -741,7 +788,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                 }
             }
             if constexpr (G::F_FINAL) {
-                // accumulators read: TMEM may be refilled by the next tile
+                // accumulator read: TMEM may be refilled by the next tile
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(b_fempty);

@@ -27,14 +27,31 @@ struct Rates {
     double hbm;        // bytes per second
 };
 
+// Rates measured on GB300: DFMA leaves at ~90% of 1.26 TFLOP/s; tensor-core
+// leaves at ~60% of the 1.89 PFLOP/s bf16 (0.93 tf32) peak divided by the
+// part products per scalar product (6 for bf16x3, 21 for the FP64
+// emulation); Strassen sums/combines on the FP64 (0.5 Gop/s) or FP32 pipe.
 Rates rates_for(ata_dtype d) {
     switch (d) {
-        case ATA_F64: return {0.60e12, 0.50e12, 6.0e12};
-        case ATA_F32_BF16X3: return {1.9e15 / 2 / 6, 35e12, 6.0e12};
-        case ATA_F32_TF32: return {1.0e15 / 2, 35e12, 6.0e12};
-        case ATA_F64_OZAKI: return {1.9e15 / 2 / 15, 0.5e12, 6.0e12};
+        case ATA_F64: return {0.57e12, 0.50e12, 6.0e12};
+        case ATA_F32_BF16X3: return {1.89e15 * 0.6 / 2 / 6, 35e12, 6.0e12};
+        case ATA_F32_TF32: return {0.93e15 * 0.6 / 2, 35e12, 6.0e12};
+        case ATA_F64_OZAKI: return {1.89e15 * 0.6 / 2 / 21, 0.5e12, 6.0e12};
     }
     return {0.6e12, 0.5e12, 6e12};
+}
+
+// Bytes the operand preparation of the tensor-core leaves moves: every leaf
+// operand element is read twice (column maxima, slicing) and written as its
+// parts.
+double prep_bytes(const Plan& P) {
+    if (P.leaf == LEAF_F64) return 0.0;
+    const TcGeom g = tc_geom(P.leaf);
+    const double in = P.in_dt == DT_F64 ? 8.0 : 4.0;
+    double elems = 0;
+    for (const LeafProduct& lp : P.products)
+        elems += (double)lp.K_pad * (lp.p_pad + (lp.out_kind == OUT_SYRK ? 0 : lp.r_pad));
+    return elems * (2.0 * in + g.parts * g.elem);
 }
 
 constexpr int64_t kWorkspaceCap = int64_t(48) << 30;  // bytes
@@ -42,8 +59,18 @@ constexpr int64_t kMaxLeafProducts = 400000;
 
 double model_time(const Plan& P, ata_dtype d) {
     const Rates r = rates_for(d);
-    return (double)P.stats.mults / r.leaf_fma + (double)P.stats.adds / r.add + 2.0 * (double)P.ws_bytes / r.hbm +
-           2e-6 * (double)(P.split_levels.size() + P.combine_levels.size() + 1);
+    // tensor-core leaves compute on whole 128 x 128 tiles
+    double leaf = (double)P.stats.mults;
+    if (P.leaf != LEAF_F64) {
+        leaf = 0;
+        for (const LeafProduct& lp : P.products) {
+            const double tiles = lp.out_kind == OUT_SYRK ? (lp.p_pad / 128.0) * (lp.p_pad / 128.0 + 1) / 2
+                                                         : (lp.p_pad / 128.0) * (lp.r_pad / 128.0);
+            leaf += tiles * 128.0 * 128.0 * lp.K_pad;
+        }
+    }
+    return leaf / r.leaf_fma + (double)P.stats.adds / r.add + 2.0 * (double)P.ws_bytes / r.hbm +
+           prep_bytes(P) / (0.5 * r.hbm) + 2e-6 * (double)(P.split_levels.size() + P.combine_levels.size() + 1);
 }
 
 // Leaf products a cutoff would create, estimated without building the plan:
@@ -99,11 +126,12 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
             return ATA_OK;
         }
     }
-    static const int cands[] = {64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048};
+    static const int cands[] = {64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
     double best = 1e300;
     int best_c = o->cutoff;
     for (int c : cands) {
         if (estimate_products(m, n, c) > kMaxLeafProducts) continue;
+        if (dtype != ATA_F64 && c < 256) continue;  // tensor-core tiles are 128 x 128
         PlanOptions t = *o;
         t.cutoff = c;
         Plan P;

@@ -324,33 +324,93 @@ __device__ __forceinline__ TS operand_value(const BindSet<NB>& bs, const Term* t
     return v;
 }
 
+// Loads a 64 (K) x 64 (column) tile of a leaf operand (a signed sum of
+// terms, zero outside each term's extent) into shared memory, tile[k][c].
+// A thread loads VEC consecutive columns at a time (16 bytes) when the term's
+// rows are 16-byte aligned and all VEC columns are inside it, else element by
+// element; a single term needs no floating-point addition.
+constexpr int PT = 64;  // prep tile edge
+
+template <typename TS, int NB>
+__device__ __forceinline__ void load_operand_tile(const BindSet<NB>& bs, const Term* __restrict__ terms, int t0,
+                                                  int nt, int K, int k0, int c0, TS (*tile)[PT + 1]) {
+    constexpr int VEC = 16 / sizeof(TS);
+    constexpr int VPR = PT / VEC;             // vectors per tile row
+    constexpr int RPP = 256 / VPR;            // rows per pass
+    const int vc = (threadIdx.x % VPR) * VEC;  // first column of this thread's vector
+    const int r0 = threadIdx.x / VPR;
+#pragma unroll
+    for (int pass = 0; pass < PT / RPP; ++pass) {
+        const int kk = r0 + pass * RPP, k = k0 + kk;
+        TS v[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) v[j] = TS(0);
+        if (k < K) {
+            for (int t = 0; t < nt; ++t) {
+                const Term& tm = terms[t0 + t];
+                if (k >= tm.rows) continue;
+                const Bind& b = bs.b[tm.inst];
+                const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
+                const TS* rowp = base + tm.off + (int64_t)k * tm.ld;
+                const int c = c0 + vc;
+                TS x[VEC];
+                if (c + VEC <= tm.cols && ((reinterpret_cast<uintptr_t>(rowp + c) & 15) == 0)) {
+                    const uint4 u = __ldg(reinterpret_cast<const uint4*>(rowp + c));
+                    *reinterpret_cast<uint4*>(x) = u;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) x[j] = (c + j < tm.cols) ? __ldg(rowp + c + j) : TS(0);
+                }
+                if (nt == 1) {
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) v[j] = tm.neg ? -x[j] : x[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) v[j] = tm.neg ? v[j] - x[j] : v[j] + x[j];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) tile[kk][vc + j] = v[j];
+    }
+}
+
 // Column maxima of |operand| (sliced modes): atomicMax on the FP64 bit
-// pattern (positive doubles order like their bits).  Block: a 64 (K) x 32
-// (column) tile.
+// pattern (positive doubles order like their bits; Inf and NaN order above
+// every finite value).  Block: a 64 (K) x 64 (column) tile.
 template <int NB, typename TS>
 __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ BindSet<NB> bs,
                                                         const LeafProduct* __restrict__ prods,
                                                         const Term* __restrict__ terms,
                                                         const TcProd* __restrict__ tcp,
                                                         const PrepTask* __restrict__ tasks) {
-    __shared__ double red[8][32];
+    __shared__ TS tile[PT][PT + 1];
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
-    const int col = threadIdx.x & 31, kr = threadIdx.x >> 5;
-    const int c = tk.c0 + col;
-    double m = 0.0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int k = tk.k0 + kr + 8 * u;
-        if (k < lp.K) m = fmax(m, (double)fabs(operand_value<TS>(bs, terms, t0, nt, k, c)));
-    }
-    red[kr][col] = m;
+    load_operand_tile<TS>(bs, terms, t0, nt, lp.K, tk.k0, tk.c0, tile);
     __syncthreads();
-    if (kr == 0) {
-        for (int i = 1; i < 8; ++i) m = fmax(m, red[i][col]);
-        unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
-        if (m > 0.0) atomicMax(ex + c, (unsigned long long)__double_as_longlong(m));
+    // magnitudes compared as bit patterns (integer operations only)
+    __shared__ unsigned long long red[4][PT];
+    const int col = threadIdx.x % PT, part = threadIdx.x / PT;
+    unsigned long long m = 0;
+    for (int k = part * (PT / 4); k < (part + 1) * (PT / 4); ++k) {
+        unsigned long long b;
+        if constexpr (sizeof(TS) == 8)
+            b = (unsigned long long)__double_as_longlong((double)tile[k][col]) & 0x7FFFFFFFFFFFFFFFull;
+        else
+            b = __float_as_uint((float)tile[k][col]) & 0x7FFFFFFFu;
+        m = b > m ? b : m;
+    }
+    red[part][col] = m;
+    __syncthreads();
+    if (threadIdx.x < PT) {
+        for (int i = 1; i < 4; ++i) m = red[i][col] > m ? red[i][col] : m;
+        if (m != 0) {
+            if constexpr (sizeof(TS) == 4) m = (unsigned long long)__double_as_longlong((double)__uint_as_float((unsigned)m));
+            unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
+            atomicMax(ex + tk.c0 + col, m);
+        }
     }
 }
 
@@ -412,8 +472,10 @@ struct PrepSrc<MODE_OZAKI> {
     using T = double;
 };
 
-// Parts of one 64 (K) x 32 (column) tile of a leaf operand, written K-major:
+// Parts of one 64 (K) x 64 (column) tile of a leaf operand, written K-major:
 // part q of column c, K index k at parts + ((q * rows_pad + c) * K_pad + k).
+// Each thread slices two (column, 8 K values) runs and writes 16 bytes per
+// part and run.
 template <int NB, int MODE>
 __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ BindSet<NB> bs,
                                                       const LeafProduct* __restrict__ prods,
@@ -421,54 +483,50 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
                                                       const TcProd* __restrict__ tcp,
                                                       const PrepTask* __restrict__ tasks) {
     using TS = typename PrepSrc<MODE>::T;
-    __shared__ TS tile[64][33];
+    __shared__ TS tile[PT][PT + 1];
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
-    {
-        const int col = threadIdx.x & 31, kr = threadIdx.x >> 5;
-        const int c = tk.c0 + col;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int kk = kr + 8 * u, k = tk.k0 + kk;
-            tile[kk][col] = (k < lp.K) ? operand_value<TS>(bs, terms, t0, nt, k, c) : TS(0);
-        }
-    }
+    load_operand_tile<TS>(bs, terms, t0, nt, lp.K, tk.k0, tk.c0, tile);
     __syncthreads();
-    const int col = threadIdx.x >> 3, kc = threadIdx.x & 7;
-    const int c = tk.c0 + col;
     const int rows_pad = tk.side ? lp.r_pad : lp.p_pad;
     const Bind& b = bs.b[lp.inst];
     char* parts = b.W + (tk.side ? lp.tc_y_off : lp.tc_x_off);
     const int64_t part_elems = (int64_t)rows_pad * lp.K_pad;
-    const int64_t base = (int64_t)c * lp.K_pad + tk.k0 + kc * 8;
-    if constexpr (MODE == MODE_TF32) {
-        float v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            uint32_t r;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(tile[kc * 8 + i][col]));
-            v[i] = __uint_as_float(r);
-        }
-        float* out = reinterpret_cast<float*>(parts);
-        *reinterpret_cast<uint4*>(out + base) = *reinterpret_cast<const uint4*>(v);
-        *reinterpret_cast<uint4*>(out + base + 4) = *reinterpret_cast<const uint4*>(v + 4);
-    } else {
-        constexpr int S = Geo<MODE>::PARTS;
-        const unsigned long long mx =
-            reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
-        const int E = col_exponent(mx);
-        int dg[8][S];
+    for (int rep = 0; rep < 2; ++rep) {
+        const int item = threadIdx.x + rep * 256;
+        const int col = item >> 3, kc = item & 7;
+        const int c = tk.c0 + col;
+        const int64_t base = (int64_t)c * lp.K_pad + tk.k0 + kc * 8;
+        if constexpr (MODE == MODE_TF32) {
+            float v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) slice_digits(tile[kc * 8 + i][col], E, dg[i]);
-        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
+            for (int i = 0; i < 8; ++i) {
+                uint32_t r;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(tile[kc * 8 + i][col]));
+                v[i] = __uint_as_float(r);
+            }
+            float* out = reinterpret_cast<float*>(parts);
+            *reinterpret_cast<uint4*>(out + base) = *reinterpret_cast<const uint4*>(v);
+            *reinterpret_cast<uint4*>(out + base + 4) = *reinterpret_cast<const uint4*>(v + 4);
+        } else {
+            constexpr int S = Geo<MODE>::PARTS;
+            const unsigned long long mx =
+                reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
+            const int E = col_exponent(mx);
+            int dg[8][S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const float unit = __int_as_float((127 - 8 * (s + 1)) << 23);  // 2^-8(s+1)
-            __nv_bfloat16 q[8];
+            for (int i = 0; i < 8; ++i) slice_digits(tile[kc * 8 + i][col], E, dg[i]);
+            __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = __float2bfloat16_rn(__int2float_rn(dg[i][s]) * unit);
-            *reinterpret_cast<uint4*>(out + s * part_elems + base) = *reinterpret_cast<const uint4*>(q);
+            for (int s = 0; s < S; ++s) {
+                const float unit = __int_as_float((127 - 8 * (s + 1)) << 23);  // 2^-8(s+1)
+                __nv_bfloat16 q[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) q[i] = __float2bfloat16_rn(__int2float_rn(dg[i][s]) * unit);
+                *reinterpret_cast<uint4*>(out + s * part_elems + base) = *reinterpret_cast<const uint4*>(q);
+            }
         }
     }
 }
@@ -946,8 +1004,8 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         if (!syrk) ex_elems += lp.r_pad;
         for (int side = 0; side < (syrk ? 1 : 2); ++side) {
             const int rows_pad = side ? lp.r_pad : lp.p_pad;
-            for (int c0 = 0; c0 < rows_pad; c0 += 32)
-                for (int k0 = 0; k0 < lp.K_pad; k0 += 64) {
+            for (int c0 = 0; c0 < rows_pad; c0 += PT)
+                for (int k0 = 0; k0 < lp.K_pad; k0 += PT) {
                     PrepTask pt;
                     pt.prod = i;
                     pt.side = (int8_t)side;

@@ -57,7 +57,9 @@ MODE_CODES = {"f64": 0, "bf16x3": 1, "tf32": 2, "ozaki": 3}
 PAIRS = {"f64": 1, "bf16x3": 6, "tf32": 1, "ozaki": 21}
 TOLERANCE = {"f64": ("componentwise", 1e-11), "ozaki": ("componentwise", 1e-11),
              "bf16x3": ("normwise", 1e-6), "tf32": ("normwise", 1e-3)}
-DEFAULT_WORKLOAD = "ata_f64_10000x10000"
+DEFAULT_WORKLOAD = "ata_ozaki_10000x10000"
+# workloads run by their own drivers (not single products)
+EXTRA_WORKLOADS = ["batched_bf16x3", "batched_f64", "serving_bf16x3", "serving_ozaki"]
 
 # Peak of the FP64 leaf arithmetic: 2 DFMA per clock per SM (the step-0
 # probe measured 1.204 TFLOP/s of DFMA on 152 SMs) at the 2070 MHz maximum
@@ -382,6 +384,29 @@ def run_ours(args):
         "gpu_launches": int(args.steps * info["n_launches"]),
         "clocks": clocks,
     }
+    if mode == "ozaki" and not args.no_plain:
+        # the plain FP64 path on the same input, same GPU, same tolerance
+        del plan
+        torch.cuda.empty_cache()
+        pf = ata.Plan(m, n, ata.ATA_F64, 0)
+        for _ in range(2):
+            pf(A, C)
+        torch.cuda.synchronize()
+        barrier(world)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(max(1, min(args.steps, 3))):
+            pf(A, C)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = max_over_ranks(torch, f0.elapsed_time(f1) / max(1, min(args.steps, 3)), world)
+        ferr = sampled_error(oracle, A_np, C, n, "componentwise", dev, torch, count=cnt)
+        line["plain_f64"] = {"value": world * eff / (fms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": fms,
+                             "cutoff": pf.info["cutoff"], "componentwise_sampled": ferr}
+        line["speedup_vs_plain_f64"] = fms / ms_max
+        del pf
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_sample(A_np, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {
@@ -396,13 +421,212 @@ def run_ours(args):
     return 0
 
 
+def _line_common(args, world, metric, value, unit, ms, mode, config):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16 (3 slices)", "tf32": "tf32",
+                                          "ozaki": "bf16 (FP64 emulation, 6 slices)"}[mode],
+            "data": "synthetic", "config": config}
+
+
+def run_batched(args, mode):
+    """Config 4: 512 independent instances, m log-U[64,4096], n log-U[32,1024],
+    U(-1,1), seed 3; one batched execution (merged task tables, one
+    persistent leaf launch, captured graph) per step."""
+    import torch
+
+    import oracle
+    import paper_1902_02104_gb300 as ata
+    from paper_1902_02104_gb300 import inputs
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    dt = np.float64 if mode in ("f64", "ozaki") else np.float32
+    mats = [a.astype(dt) for a in inputs.batch(512, seed=3)]
+    plans = [ata.Plan(a.shape[0], a.shape[1], MODE_CODES[mode], 0) for a in mats]
+    As = [torch.from_numpy(a).to(dev) for a in mats]
+    Cs = [torch.empty(a.shape[1] * (a.shape[1] + 1) // 2, dtype=torch.float64, device=dev) for a in mats]
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ata.ata_execute_batched(plans, As, Cs)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_smi_index(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ata.ata_execute_batched(plans, As, Cs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = max_over_ranks(torch, e0.elapsed_time(e1) / args.steps, world)
+    eff = sum(effective_flops(a.shape[0], a.shape[1]) for a in mats)
+    kind, tol = TOLERANCE[mode]
+    errs = []
+    for i in range(0, 512, 64):  # every 64th instance against the full oracle
+        ref = oracle.ata_packed(mats[i])
+        got = Cs[i].cpu().numpy()
+        if kind == "normwise":
+            errs.append(oracle.normwise_error(got, ref, mats[i].shape[1]))
+        else:
+            errs.append(oracle.componentwise_error(got, ref, oracle.abs_gram_packed(mats[i])))
+    mults = sum(p.info["mults"] for p in plans)
+    leaf_flops = 2.0 * mults * PAIRS[mode]
+    achieved = leaf_flops / (ms / 1e3) / 1e12
+    if mode == "f64":
+        peak, peak_src, bound = FP64_ALU_PEAK_TFLOPS, "derived DFMA peak", "alu"
+    else:
+        peak, peak_src = tensor_peak(mode)
+        bound = "tensor"
+    # end to end: inputs from pinned host memory, results back, every step
+    hostA = [torch.from_numpy(a).pin_memory() for a in mats]
+    hostC = [torch.empty(c.numel(), dtype=torch.float64).pin_memory() for c in Cs]
+    def e2e_step():
+        for h, d in zip(hostA, As):
+            d.copy_(h, non_blocking=True)
+        ata.ata_execute_batched(plans, As, Cs)
+        for h, d in zip(hostC, Cs):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 3))):
+        e2e_step()
+    t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / max(1, min(args.steps, 3)), world)
+    line = _line_common(args, world, "effective TFLOP/s (m*n^2 FMAs) of C = A^t A, 512 batched instances",
+                        world * eff / (ms / 1e3) / 1e12, "TFLOP/s", ms, mode,
+                        {"workload": f"batched_{mode}", "instances": 512, "m_range": [64, 4096],
+                         "n_range": [32, 1024], "generator": "uniform(-1,1) seed 3", "cutoff": "autotuned per shape",
+                         "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (%.0f MB)" % (
+                             sum(a.nbytes for a in mats) / 2**20)})
+    line["error"] = {kind + "_max_of_8": max(errs), "tolerance": tol}
+    line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": "whole batched step (leaf flops / step time)", "flops_per_launch": leaf_flops}
+    line["e2e"] = {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s",
+                   "h2d_bytes_per_step": int(sum(a.nbytes for a in mats)),
+                   "d2h_bytes_per_step": int(sum(c.numel() * 8 for c in Cs))}
+    line["gpu_launches"] = None
+    line["clocks"] = clocks
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def run_serving(args, mode):
+    """Config 5: Poisson arrivals at --rate for --duration seconds; requests
+    draw matrices from a 256-entry pool (m log-U[128,8192], n log-U[64,2048],
+    N(0,1)); admission by a 40 GB budget; plans resident after warm-up."""
+    import torch
+
+    import oracle
+    import paper_1902_02104_gb300 as ata
+    from paper_1902_02104_gb300 import inputs
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    dt = np.float64 if mode in ("f64", "ozaki") else np.float32
+    rng, pool = inputs.serving_pool(256, seed=4)
+    pool = [a.astype(dt) for a in pool]
+    As = [torch.from_numpy(a).to(dev) for a in pool]
+    nring = 2  # output buffers per pool entry
+    Cs = [[torch.empty(a.shape[1] * (a.shape[1] + 1) // 2, dtype=torch.float64, device=dev) for _ in range(nring)]
+          for a in pool]
+    srv = ata.Server(40 << 30, MODE_CODES[mode], max_inflight=16)
+    # warm-up: every pool shape once (plans become resident)
+    tick = [srv.submit(As[i], Cs[i][0]) for i in range(len(pool))]
+    for t in tick:
+        srv.poll(t, 600_000_000)
+    arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=4)
+    which = rng.integers(0, len(pool), size=arrivals.size)
+    srv.reset_stats()
+    pending = []
+    use = [0] * len(pool)
+    t0 = time.perf_counter()
+    for t_arr, i in zip(arrivals, which):
+        while time.perf_counter() - t0 < t_arr:
+            pass
+        c = Cs[i][use[i] % nring]
+        use[i] += 1
+        pending.append(srv.submit(As[i], c))
+    for t in pending:
+        srv.poll(t, 600_000_000)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    eff = sum(effective_flops(*pool[i].shape) for i in which)
+    # latency of the timed requests only: the server keeps all; recompute from the tail
+    kind, tol = TOLERANCE[mode]
+    # correctness: a few requests run alone, then compared with the oracle
+    errs = []
+    for i in range(0, 256, 64):
+        t = srv.submit(As[i], Cs[i][0])
+        srv.poll(t, 600_000_000)
+        got = Cs[i][0].cpu().numpy()
+        ref = oracle.ata_packed(pool[i])
+        if kind == "normwise":
+            errs.append(oracle.normwise_error(got, ref, pool[i].shape[1]))
+        else:
+            errs.append(oracle.componentwise_error(got, ref, oracle.abs_gram_packed(pool[i])))
+    srv.close()
+    # the plain FP64 path on the same pool: its service time per request, run
+    # one request at a time on one stream (capacity, not served under load)
+    fp64 = None
+    if not args.no_plain:
+        idx = list(range(0, 256, 8))
+        svc = []
+        for i in idx:
+            a = pool[i].astype(np.float64)
+            pf = ata.Plan(a.shape[0], a.shape[1], ata.ATA_F64, 0)
+            Ad = torch.from_numpy(a).to(dev)
+            Cd = torch.empty(a.shape[1] * (a.shape[1] + 1) // 2, dtype=torch.float64, device=dev)
+            pf(Ad, Cd)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record()
+            pf(Ad, Cd)
+            f1.record()
+            torch.cuda.synchronize()
+            svc.append(f0.elapsed_time(f1))
+            del pf, Ad, Cd
+        mean_ms = float(np.mean(svc))
+        eff_mean = float(np.mean([effective_flops(*pool[i].shape) for i in idx]))
+        fp64 = {"mean_service_ms": mean_ms, "max_rate_per_s": 1e3 / mean_ms,
+                "effective_tflops_at_capacity": eff_mean / (mean_ms / 1e3) / 1e12,
+                "sample": f"{len(idx)} pool shapes, one request at a time"}
+    line = _line_common(args, world, "sustained effective TFLOP/s of served A^t A requests; p50/p99 latency",
+                        world * eff / wall / 1e12, "TFLOP/s", wall * 1e3, mode,
+                        {"workload": f"serving_{mode}", "rate_per_s": args.rate, "duration_s": args.duration,
+                         "requests": int(arrivals.size), "pool": 256, "m_range": [128, 8192],
+                         "n_range": [64, 2048], "budget_bytes": 40 << 30, "max_inflight": 16,
+                         "parallelism": f"replicas{world}"})
+    line["latency_us"] = {"p50": st["p50_us"], "p99": st["p99_us"], "completed": st["completed"]}
+    line["offered_effective_tflops"] = eff / args.duration / 1e12
+    line["plain_f64_capacity"] = fp64
+    line["error"] = {kind + "_max_of_4": max(errs), "tolerance": tol}
+    line["roofline"] = None
+    line["e2e"] = None
+    line["gpu_launches"] = None
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + EXTRA_WORKLOADS, default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cutoff", type=int, default=None, help="override the workload's cutoff")
@@ -411,6 +635,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batched_"):
+        return run_batched(args, args.workload.split("_", 1)[1])
+    if args.workload.startswith("serving_"):
+        return run_serving(args, args.workload.split("_", 1)[1])
     return run_ours(args)
 
 

@@ -146,6 +146,14 @@ typedef struct {
 ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n,
                                 ata_dtype dtype, const ata_plan_options* opts);
 
+/* Host-side check of the plan ata_plan_create_opts(m, n, dtype, opts) would
+ * build (no device call): every read and write of every task stays inside
+ * A (m x n), the workspace and C, and the tasks write every entry of the
+ * packed triangle exactly once (the latter for n <= 4096).  Returns ATA_OK,
+ * or ATA_EINVAL with the first violation in ata_last_error_message(). */
+ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype,
+                          const ata_plan_options* opts);
+
 /* ata_plan_query with explicit options. */
 ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype,
                                const ata_plan_options* opts,
@@ -261,6 +269,9 @@ ata_status ata_poll(ata_server srv, ata_ticket ticket, int timeout_us);
  * the scheduler), in microseconds, and the count. */
 ata_status ata_server_stats(ata_server srv, double* p50_us, double* p99_us,
                             int64_t* completed);
+
+/* Forget the latencies recorded so far (e.g. after a warm-up phase). */
+ata_status ata_server_reset_stats(ata_server srv);
 
 /* Stop the scheduler after draining queued work, then free everything. */
 void ata_server_destroy(ata_server srv);

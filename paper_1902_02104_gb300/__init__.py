@@ -78,6 +78,7 @@ def load():
         "ata_plan_query_opts": ([i64, i64, i32, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanInfo)], i32),
         "ata_plan_create": ([ctypes.POINTER(vp), i64, i64, i32, i32], i32),
         "ata_plan_create_opts": ([ctypes.POINTER(vp), i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
+        "ata_plan_check": ([i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
         "ata_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i32),
         "ata_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "ata_execute": ([vp, vp, i64, dp, vp], i32),
@@ -95,6 +96,7 @@ def load():
         "ata_server_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(i64)], i32),
         "ata_server_destroy": ([vp], None),
+        "ata_server_reset_stats": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -129,6 +131,12 @@ def ata_plan_query(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> di
     o = _opts(cutoff, **opts)
     _check(load().ata_plan_query_opts(m, n, _dtype_code(dtype), ctypes.byref(o), ctypes.byref(info)))
     return info.as_dict()
+
+
+def ata_plan_check(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts):
+    """Host-side bounds and coverage check of the plan (raises AtaError)."""
+    o = _opts(cutoff, **opts)
+    _check(load().ata_plan_check(m, n, _dtype_code(dtype), ctypes.byref(o)))
 
 
 def _stream_handle(stream):
@@ -307,6 +315,9 @@ class Server:
         p50, p99, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
         _check(load().ata_server_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n)))
         return {"p50_us": p50.value, "p99_us": p99.value, "completed": n.value}
+
+    def reset_stats(self):
+        _check(load().ata_server_reset_stats(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):

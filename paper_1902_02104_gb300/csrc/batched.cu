@@ -108,7 +108,7 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
         std::vector<Bind> binds;
         for (int i = g0; i < g1; ++i) {
             const Plan& P = plan_of(plans[i]);
-            binds.push_back(Bind{A[i], C_packed[i], plan_workspace(plans[i]), P.n});
+            binds.push_back(make_bind(plans[i], A[i], lda[i], C_packed[i]));
         }
         ata_status st = launch_via_graph(it->second->tables, binds.data(), (int)binds.size(), &it->second->graph, s);
         if (st != ATA_OK) return st;

@@ -15,9 +15,13 @@ struct Bind {
     double* C;
     char* W;
     int64_t n;
+    // extents for the optional self-check of every global access (check != 0):
+    // elements of A, bytes of W, elements of C
+    int64_t a_elems, w_bytes, c_elems;
+    int64_t check;
 };
 
-constexpr int kMaxBatchBind = 512;  // instances per batched launch (16 KB of parameters)
+constexpr int kMaxBatchBind = 256;  // instances per batched launch (16 KB of parameters)
 
 template <int NB>
 struct BindSet {
@@ -41,13 +45,16 @@ constexpr int kMaxTerms = 32;     // terms per operand the leaf kernels accept
 
 // `binds` holds nb <= kMaxBatchBind instances (nb == 1 uses the single-plan
 // instantiation of each kernel).
-cudaError_t launch_leaf_f64(const Bind* binds, int nb, const LeafProduct* prods, const Term* terms, const LeafTile* tiles,
+// `status` receives a nonzero code when a self-checked access falls outside its
+// buffer (the access is skipped): 11 leaf read, 12 leaf write, 21 split read,
+// 22 split write, 31 combine read, 32 combine write.
+cudaError_t launch_leaf_f64(int* status, const Bind* binds, int nb, const LeafProduct* prods, const Term* terms, const LeafTile* tiles,
                             int ntiles, int* counter, int grid, cudaStream_t s);
 
-cudaError_t launch_split(const Bind* binds, int nb, const SplitTask* tasks, const Chunk* chunks, int nchunks, int8_t src_dt,
+cudaError_t launch_split(int* status, const Bind* binds, int nb, const SplitTask* tasks, const Chunk* chunks, int nchunks, int8_t src_dt,
                          int8_t dst_dt, cudaStream_t s);
 
-cudaError_t launch_combine(const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks, int nchunks,
+cudaError_t launch_combine(int* status, const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks, int nchunks,
                            cudaStream_t s);
 
 // Resident blocks of the FP64 leaf kernel per SM (for persistent grids).

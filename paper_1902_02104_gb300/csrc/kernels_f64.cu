@@ -29,11 +29,25 @@ __device__ __forceinline__ const T* term_ptr(const Bind& b, const Term& t) {
 // each term's valid extent (implicit zero padding of uneven blocks).  A
 // single term (every materialised operand) needs no FP64 addition: its sign
 // is applied to the bit pattern, so the FP64 pipe only runs the leaf DFMAs.
+// Self-check of a global access (only when the binding asks for it): the
+// element index must lie inside its buffer; otherwise the access is skipped
+// and `code` is recorded in *status.
+__device__ __forceinline__ bool in_bounds(const Bind& b, int8_t buf, int64_t idx, int es, int* status, int code) {
+    if (!b.check) return true;
+    const int64_t lim = buf == BUF_A ? b.a_elems : buf == BUF_W ? b.w_bytes / es : b.c_elems;
+    if (idx >= 0 && idx < lim) return true;
+    atomicCAS(status, 0, code);
+    return false;
+}
+
 template <int NB>
-__device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* ts, int nt, int k, int c) {
+__device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* ts, int nt, int k, int c,
+                                             int* status) {
     if (nt == 1) {
         const Term& tm = ts[0];
         if (k >= tm.rows || c >= tm.cols) return 0.0;
+        const int64_t idx = tm.off + (int64_t)k * tm.ld + c;
+        if (!in_bounds(bs.b[tm.inst], tm.buf, idx, 8, status, 11)) return 0.0;
         const double x = __ldg(term_ptr<double>(bs.b[tm.inst], tm) + (int64_t)k * tm.ld + c);
         return __longlong_as_double(__double_as_longlong(x) ^ ((long long)tm.neg << 63));
     }
@@ -41,6 +55,8 @@ __device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* 
     for (int t = 0; t < nt; ++t) {
         const Term& tm = ts[t];
         if (k < tm.rows && c < tm.cols) {
+            const int64_t idx = tm.off + (int64_t)k * tm.ld + c;
+            if (!in_bounds(bs.b[tm.inst], tm.buf, idx, 8, status, 11)) continue;
             const double x = __ldg(term_ptr<double>(bs.b[tm.inst], tm) + (int64_t)k * tm.ld + c);
             v = tm.neg ? v - x : v + x;
         }
@@ -69,7 +85,7 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
                                                             const LeafProduct* __restrict__ prods,
                                                             const Term* __restrict__ terms,
                                                             const LeafTile* __restrict__ tiles, int ntiles,
-                                                            int* __restrict__ counter) {
+                                                            int* __restrict__ counter, int* __restrict__ status) {
     __shared__ __align__(16) double Xs[2][BK][TILE];
     __shared__ __align__(16) double Ys[2][BK][TILE];
     __shared__ Term sx[kMaxTerms], sy[kMaxTerms];
@@ -118,8 +134,8 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
                 const int idx = tid + e * NTHREADS;
                 const int kk = idx / TILE, c = idx % TILE;
                 const int k = k0 + kk;
-                px[e] = (k < K) ? operand_at(bs, sx, nx, k, i0 + c) : 0.0;
-                py[e] = (k < K) ? operand_at(bs, sy, ny, k, j0 + c) : 0.0;
+                px[e] = (k < K) ? operand_at(bs, sx, nx, k, i0 + c, status) : 0.0;
+                py[e] = (k < K) ? operand_at(bs, sy, ny, k, j0 + c, status) : 0.0;
             }
         };
         auto stash = [&](int buf) {
@@ -173,11 +189,13 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
                     const int j = j0 + col0 + 8 * b;
                     if (j >= sp.out_cols) continue;
                     if (sp.out_kind == OUT_DENSE) {
-                        reinterpret_cast<double*>(bind.W)[sp.out_off + (int64_t)i * sp.out_ld + j] = acc[a][b];
+                        const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
+                        if (in_bounds(bind, BUF_W, idx, 8, status, 12)) reinterpret_cast<double*>(bind.W)[idx] = acc[a][b];
                     } else {
                         const int64_t gi = (int64_t)sp.ci0 + i, gj = (int64_t)sp.cj0 + j;
                         if (sp.out_kind == OUT_SYRK && gj < gi) continue;
-                        bind.C[packed_start(gi, bind.n) + (gj - gi)] = acc[a][b];
+                        const int64_t idx = packed_start(gi, bind.n) + (gj - gi);
+                        if (in_bounds(bind, BUF_C, idx, 8, status, 12)) bind.C[idx] = acc[a][b];
                     }
                 }
             }
@@ -193,7 +211,7 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
 template <int NB, typename TS, typename TD>
 __global__ void __launch_bounds__(256) split_kernel(const __grid_constant__ BindSet<NB> bs,
                                                     const SplitTask* __restrict__ tasks,
-                                                    const Chunk* __restrict__ chunks) {
+                                                    const Chunk* __restrict__ chunks, int* __restrict__ status) {
     const Chunk ch = chunks[blockIdx.x];
     const SplitTask& st = tasks[ch.task];
     const Bind& bind = bs.b[st.inst];
@@ -213,10 +231,18 @@ __global__ void __launch_bounds__(256) split_kernel(const __grid_constant__ Bind
             for (int cb = 0; cb < 2; ++cb) {
                 const int rr = kb * K1 + k, cc = cb * c1 + c;
                 TD v = 0;
-                if (rr < srows && cc < scols) v = (TD)src[(int64_t)rr * ld + cc];
+                if (rr < srows && cc < scols &&
+                    in_bounds(bind, st.src.buf, st.src.off + (int64_t)rr * ld + cc, sizeof(TS), status, 21))
+                    v = (TD)src[(int64_t)rr * ld + cc];
                 B[2 * kb + cb] = neg ? -v : v;
             }
         const int64_t o = (int64_t)k * c1 + c;
+        if (bind.check) {
+            bool ok = true;
+            for (int q = 0; q < st.nout; ++q)
+                ok &= in_bounds(bind, BUF_W, st.out_off[q] + o, sizeof(TD), status, 22);
+            if (!ok) continue;
+        }
         if (st.variant == 0) {
             if (st.side == 0) {  // left factor X^t: M1 M2 M5 M6 M7
                 W[st.out_off[0] + o] = B[0] + B[3];
@@ -258,7 +284,7 @@ __global__ void __launch_bounds__(256) split_kernel(const __grid_constant__ Bind
 template <int NB>
 __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ BindSet<NB> bs,
                                                       const CombineTask* __restrict__ tasks,
-                                                      const Chunk* __restrict__ chunks) {
+                                                      const Chunk* __restrict__ chunks, int* __restrict__ status) {
     const Chunk ch = chunks[blockIdx.x];
     const CombineTask& ct = tasks[ch.task];
     const Bind& bind = bs.b[ct.inst];
@@ -271,7 +297,8 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Bi
         const int64_t o = (int64_t)i * r1 + j;
         double m[7];
 #pragma unroll
-        for (int t = 0; t < 7; ++t) m[t] = M[t * msz + o];
+        for (int t = 0; t < 7; ++t)
+            m[t] = in_bounds(bind, BUF_W, ct.m_off + t * msz + o, 8, status, 31) ? M[t * msz + o] : 0.0;
         double d[4];
         if (ct.variant == 0) {
             d[0] = m[0] - m[4] + m[6] + m[3];  // D11 = M1 - M5 + M7 + M4
@@ -291,10 +318,12 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Bi
             const int ii = (q >> 1) * p1 + i, jj = (q & 1) * r1 + j;
             if (ii >= p || jj >= r) continue;
             if (ct.dst_kind == OUT_DENSE) {
-                reinterpret_cast<double*>(bind.W)[ct.dst_off + (int64_t)ii * ct.dst_ld + jj] = d[q];
+                const int64_t idx = ct.dst_off + (int64_t)ii * ct.dst_ld + jj;
+                if (in_bounds(bind, BUF_W, idx, 8, status, 32)) reinterpret_cast<double*>(bind.W)[idx] = d[q];
             } else {
                 const int64_t gi = (int64_t)ct.ci0 + ii, gj = (int64_t)ct.cj0 + jj;
-                bind.C[packed_start(gi, bind.n) + (gj - gi)] = d[q];
+                const int64_t idx = packed_start(gi, bind.n) + (gj - gi);
+                if (in_bounds(bind, BUF_C, idx, 8, status, 32)) bind.C[idx] = d[q];
             }
         }
     }
@@ -309,14 +338,15 @@ BindSet<NB> make_set(const Bind* binds, int nb) {
 
 }  // namespace
 
-cudaError_t launch_leaf_f64(const Bind* binds, int nb, const LeafProduct* prods, const Term* terms,
+cudaError_t launch_leaf_f64(int* status, const Bind* binds, int nb, const LeafProduct* prods, const Term* terms,
                             const LeafTile* tiles, int ntiles, int* counter, int grid, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (nb <= 1)
-        leaf_f64_kernel<1><<<grid, NTHREADS, 0, s>>>(make_set<1>(binds, nb), prods, terms, tiles, ntiles, counter);
+        leaf_f64_kernel<1><<<grid, NTHREADS, 0, s>>>(make_set<1>(binds, nb), prods, terms, tiles, ntiles, counter,
+                                                     status);
     else if (nb <= kMaxBatchBind)
         leaf_f64_kernel<kMaxBatchBind><<<grid, NTHREADS, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), prods, terms,
-                                                                 tiles, ntiles, counter);
+                                                                 tiles, ntiles, counter, status);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -329,36 +359,37 @@ int leaf_f64_blocks_per_sm() {
 }
 
 template <int NB>
-static cudaError_t split_dispatch(const BindSet<NB>& bs, const SplitTask* tasks, const Chunk* chunks, int nchunks,
-                                  int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
+static cudaError_t split_dispatch(int* status, const BindSet<NB>& bs, const SplitTask* tasks, const Chunk* chunks,
+                                  int nchunks, int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
     if (src_dt == DT_F64 && dst_dt == DT_F64)
-        split_kernel<NB, double, double><<<nchunks, 256, 0, s>>>(bs, tasks, chunks);
+        split_kernel<NB, double, double><<<nchunks, 256, 0, s>>>(bs, tasks, chunks, status);
     else if (src_dt == DT_F32 && dst_dt == DT_F32)
-        split_kernel<NB, float, float><<<nchunks, 256, 0, s>>>(bs, tasks, chunks);
+        split_kernel<NB, float, float><<<nchunks, 256, 0, s>>>(bs, tasks, chunks, status);
     else if (src_dt == DT_F32 && dst_dt == DT_F64)
-        split_kernel<NB, float, double><<<nchunks, 256, 0, s>>>(bs, tasks, chunks);
+        split_kernel<NB, float, double><<<nchunks, 256, 0, s>>>(bs, tasks, chunks, status);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_split(const Bind* binds, int nb, const SplitTask* tasks, const Chunk* chunks, int nchunks,
-                         int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
+cudaError_t launch_split(int* status, const Bind* binds, int nb, const SplitTask* tasks, const Chunk* chunks,
+                         int nchunks, int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
-    if (nb <= 1) return split_dispatch<1>(make_set<1>(binds, nb), tasks, chunks, nchunks, src_dt, dst_dt, s);
+    if (nb <= 1) return split_dispatch<1>(status, make_set<1>(binds, nb), tasks, chunks, nchunks, src_dt, dst_dt, s);
     if (nb <= kMaxBatchBind)
-        return split_dispatch<kMaxBatchBind>(make_set<kMaxBatchBind>(binds, nb), tasks, chunks, nchunks, src_dt,
-                                             dst_dt, s);
+        return split_dispatch<kMaxBatchBind>(status, make_set<kMaxBatchBind>(binds, nb), tasks, chunks, nchunks,
+                                             src_dt, dst_dt, s);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_combine(const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks, int nchunks,
-                           cudaStream_t s) {
+cudaError_t launch_combine(int* status, const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks,
+                           int nchunks, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
     if (nb <= 1)
-        combine_kernel<1><<<nchunks, 256, 0, s>>>(make_set<1>(binds, nb), tasks, chunks);
+        combine_kernel<1><<<nchunks, 256, 0, s>>>(make_set<1>(binds, nb), tasks, chunks, status);
     else if (nb <= kMaxBatchBind)
-        combine_kernel<kMaxBatchBind><<<nchunks, 256, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), tasks, chunks);
+        combine_kernel<kMaxBatchBind><<<nchunks, 256, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), tasks, chunks,
+                                                              status);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -143,6 +143,10 @@ extern "C" ata_status ata_execute_static_scratch(int64_t m, int64_t n, const dou
     t.ntiles = (int)h.tiles.size();
     t.split_lv = h.split_lv;
     t.comb_lv = h.comb_lv;
-    Bind b{A, C_packed, scratch + o_ws, n};
+    Bind b{};
+    b.A = A;
+    b.C = C_packed;
+    b.W = scratch + o_ws;
+    b.n = n;
     return enqueue_tables(t, &b, 1, s);
 }

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -225,10 +226,12 @@ static void device_params(int* sms, int* per_sm) {
 ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s, const cudaEvent_t* ev) {
     int sms = 1, per_sm = 1;
     device_params(&sms, &per_sm);
+    int* fstatus = t.counter + 1;  // status word of the FP64 / split / combine kernels
     if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
     for (size_t l = 0; l < t.split_lv.size(); ++l) {
         const LevelRange& lr = t.split_lv[l];
-        ATA_CUDA(launch_split(binds, nb, t.split, t.split_chunks + lr.chunk0, lr.nchunks, lr.src_dt, lr.dst_dt, s));
+        ATA_CUDA(launch_split(fstatus, binds, nb, t.split, t.split_chunks + lr.chunk0, lr.nchunks, lr.src_dt,
+                              lr.dst_dt, s));
     }
     if (t.ntiles > 0) ATA_CUDA(cudaMemsetAsync(t.counter, 0, sizeof(int), s));
     if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -236,7 +239,7 @@ ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cuda
         if (t.leaf == LEAF_F64) {
             if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
             const int grid = std::max(1, std::min(t.ntiles, sms * per_sm));
-            ATA_CUDA(launch_leaf_f64(binds, nb, t.prods, t.terms, t.tiles, t.ntiles, t.counter, grid, s));
+            ATA_CUDA(launch_leaf_f64(fstatus, binds, nb, t.prods, t.terms, t.tiles, t.ntiles, t.counter, grid, s));
         } else {
             ata_status st = launch_leaf_tc(t, binds, nb, s, ev ? ev[2] : nullptr);
             if (st != ATA_OK) return st;
@@ -246,7 +249,7 @@ ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cuda
     if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     for (int l = (int)t.comb_lv.size() - 1; l >= 0; --l) {
         const LevelRange& lr = t.comb_lv[l];
-        ATA_CUDA(launch_combine(binds, nb, t.comb, t.comb_chunks + lr.chunk0, lr.nchunks, s));
+        ATA_CUDA(launch_combine(fstatus, binds, nb, t.comb, t.comb_chunks + lr.chunk0, lr.nchunks, s));
     }
     if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal));
     return ATA_OK;
@@ -338,6 +341,7 @@ struct ata_plan_s {
     DeviceTables tables;
     GraphCache graph;
     std::mutex mu;
+    int64_t check = 0;          // self-checked kernels (ATA_CHECK_BOUNDS=1 at creation)
     // staging for ata_execute_host
     void* stage_A = nullptr;
     double* stage_C = nullptr;
@@ -491,6 +495,108 @@ ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype, const ata_
     return ATA_OK;
 }
 
+ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
+    if (!opts) return fail(ATA_EINVAL, "NULL argument");
+    PlanOptions o;
+    ata_status st = make_options(m, n, dtype, *opts, &o);
+    if (st != ATA_OK) return st;
+    if (opts->cutoff == 0) {
+        st = autotune_cutoff(m, n, dtype, o.variant, &o);
+        if (st != ATA_OK) return st;
+    }
+    Plan P;
+    std::string err;
+    if (!build_plan(m, n, o, &P, &err)) return fail(ATA_EINVAL, err);
+    const int64_t ws = P.ws_bytes;
+    char msg[256];
+    auto term_ok = [&](const Term& t, const char* what) -> bool {
+        if (t.rows <= 0 || t.cols <= 0) return true;
+        if (t.buf == BUF_A) {
+            const int64_t r0 = P.n ? t.off / P.n : 0, c0 = P.n ? t.off % P.n : 0;
+            if (t.ld != P.n || r0 + t.rows > P.m || c0 + t.cols > P.n) {
+                snprintf(msg, sizeof msg, "%s: A term rows %lld+%d cols %lld+%d outside %lldx%lld", what,
+                         (long long)r0, t.rows, (long long)c0, t.cols, (long long)P.m, (long long)P.n);
+                return false;
+            }
+        } else {
+            const int es = t.dt == DT_F64 ? 8 : 4;
+            const int64_t end = (t.off + (int64_t)(t.rows - 1) * t.ld + t.cols) * es;
+            if (t.off < 0 || t.cols > t.ld || end > ws) {
+                snprintf(msg, sizeof msg, "%s: W term ends at byte %lld of %lld", what, (long long)end,
+                         (long long)ws);
+                return false;
+            }
+        }
+        return true;
+    };
+    const bool cover = n <= 4096;
+    std::vector<uint8_t> hits(cover ? (size_t)(n * (n + 1) / 2) : 0, 0);
+    auto mark = [&](int64_t i, int64_t j) -> bool {
+        if (i < 0 || j < i || j >= n) return false;
+        if (cover) {
+            uint8_t& h = hits[(size_t)(i * n - i * (i - 1) / 2 + (j - i))];
+            if (h) return false;
+            h = 1;
+        }
+        return true;
+    };
+    for (const LeafProduct& lp : P.products) {
+        for (int t = 0; t < lp.nx; ++t)
+            if (!term_ok(P.terms[lp.x0 + t], "leaf X")) return fail(ATA_EINVAL, msg);
+        for (int t = 0; t < lp.ny; ++t)
+            if (!term_ok(P.terms[lp.y0 + t], "leaf Y")) return fail(ATA_EINVAL, msg);
+        if (lp.nx > kMaxTerms || lp.ny > kMaxTerms) return fail(ATA_EINVAL, "too many fused terms");
+        if (lp.out_rows > lp.p || lp.out_cols > lp.r) return fail(ATA_EINVAL, "leaf extent beyond its product");
+        if (lp.out_kind == OUT_DENSE) {
+            const int64_t end = (lp.out_off + (int64_t)(lp.out_rows - 1) * lp.out_ld + lp.out_cols) * 8;
+            if (lp.out_cols > lp.out_ld || end > ws) return fail(ATA_EINVAL, "leaf dense output beyond workspace");
+        } else {
+            for (int64_t i = 0; i < lp.out_rows; ++i)
+                for (int64_t j = (lp.out_kind == OUT_SYRK ? i : 0); j < lp.out_cols; ++j)
+                    if (!mark(lp.ci0 + i, lp.cj0 + j)) {
+                        snprintf(msg, sizeof msg, "leaf writes C(%lld,%lld) outside or twice", (long long)(lp.ci0 + i),
+                                 (long long)(lp.cj0 + j));
+                        return fail(ATA_EINVAL, msg);
+                    }
+        }
+        if (P.leaf != LEAF_F64) {
+            const TcGeom g = tc_geom(P.leaf);
+            if ((lp.tc_x_off + (int64_t)g.parts * lp.p_pad * lp.K_pad * g.elem) > ws ||
+                (lp.tc_y_off + (int64_t)g.parts * lp.r_pad * lp.K_pad * g.elem) > ws ||
+                lp.K_pad % 64 || lp.p_pad % kTcTile || lp.r_pad % kTcTile || lp.K_pad < lp.K)
+                return fail(ATA_EINVAL, "tensor-core part buffers outside the workspace");
+        }
+    }
+    for (auto& lv : P.split_levels)
+        for (const SplitTask& stk : lv) {
+            if (!term_ok(stk.src, "split source")) return fail(ATA_EINVAL, msg);
+            const int es = stk.dst_dt == DT_F64 ? 8 : 4;
+            for (int k = 0; k < stk.nout; ++k)
+                if ((stk.out_off[k] + (int64_t)stk.K1 * stk.c1) * es > ws)
+                    return fail(ATA_EINVAL, "split output beyond workspace");
+        }
+    for (auto& lv : P.combine_levels)
+        for (const CombineTask& ct : lv) {
+            if ((ct.m_off + 7LL * ct.p1 * ct.r1) * 8 > ws) return fail(ATA_EINVAL, "combine sources beyond workspace");
+            if (ct.dst_kind == OUT_DENSE) {
+                if ((ct.dst_off + (int64_t)(ct.p - 1) * ct.dst_ld + ct.r) * 8 > ws || ct.r > ct.dst_ld)
+                    return fail(ATA_EINVAL, "combine output beyond workspace");
+            } else {
+                for (int64_t i = 0; i < ct.p; ++i)
+                    for (int64_t j = 0; j < ct.r; ++j)
+                        if (!mark(ct.ci0 + i, ct.cj0 + j)) {
+                            snprintf(msg, sizeof msg, "combine writes C(%lld,%lld) outside or twice",
+                                     (long long)(ct.ci0 + i), (long long)(ct.cj0 + j));
+                            return fail(ATA_EINVAL, msg);
+                        }
+            }
+        }
+    if (cover)
+        for (size_t k = 0; k < hits.size(); ++k)
+            if (!hits[k]) return fail(ATA_EINVAL, "an entry of C is never written");
+    return ATA_OK;
+}
+
 ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
     if (!out || !opts) return fail(ATA_EINVAL, "NULL argument");
     *out = nullptr;
@@ -509,6 +615,10 @@ ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype d
     if (!leaf_supported(p->plan.leaf)) return fail(ATA_EUNSUPPORTED, "leaf kind not built into this library");
     p->id = g_plan_ids.fetch_add(1);
     p->dtype = dtype;
+    {
+        const char* chk = getenv("ATA_CHECK_BOUNDS");
+        p->check = (chk && chk[0] == '1') ? 1 : 0;
+    }
     ATA_CUDA(cudaGetDevice(&p->device));
     if (p->plan.ws_bytes > 0) {
         cudaError_t e = cudaMalloc(&p->ws, p->plan.ws_bytes);
@@ -559,7 +669,7 @@ ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_pack
         st = rebuild_tables(plan, lda);
         if (st != ATA_OK) return st;
     }
-    Bind b{A, C_packed, plan->ws, n};
+    Bind b = make_bind(plan, A, lda, C_packed);
     return launch_via_graph(plan->tables, &b, 1, &plan->graph, static_cast<cudaStream_t>(stream));
 }
 
@@ -622,8 +732,9 @@ ata_status ata_plan_stage_times(ata_plan plan, float* ms) {
 ata_status ata_plan_device_status(ata_plan plan, int* code) {
     if (!plan || !code) return fail(ATA_EINVAL, "NULL argument");
     *code = 0;
-    if (!plan->tables.status) return ATA_OK;
-    ATA_CUDA(cudaMemcpy(code, plan->tables.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (plan->tables.status) ATA_CUDA(cudaMemcpy(code, plan->tables.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*code == 0 && plan->tables.counter)
+        ATA_CUDA(cudaMemcpy(code, plan->tables.counter + 1, sizeof(int), cudaMemcpyDeviceToHost));
     return ATA_OK;
 }
 
@@ -639,6 +750,18 @@ void ata_plan_destroy(ata_plan plan) {
 // ---------------------------------------------------------------------------
 // Accessors used by the batched and serving layers.
 namespace ata {
+Bind make_bind(ata_plan p, const void* A, int64_t lda, double* C) {
+    Bind b{};
+    b.A = A;
+    b.C = C;
+    b.W = p->ws;
+    b.n = p->plan.n;
+    b.a_elems = p->plan.m > 0 ? (p->plan.m - 1) * lda + p->plan.n : 0;
+    b.w_bytes = p->plan.ws_bytes;
+    b.c_elems = p->plan.n * (p->plan.n + 1) / 2;
+    b.check = p->check;
+    return b;
+}
 const Plan& plan_of(ata_plan p) { return p->plan; }
 uint64_t plan_id(ata_plan p) { return p->id; }
 char* plan_workspace(ata_plan p) { return p->ws; }

@@ -41,3 +41,14 @@ def test_null_plan_rejected_without_device_work():
     assert lib.ata_execute_batched(None, -1, None, None, None, None) == ata.ATA_EINVAL
     assert lib.ata_execute_batched(None, 0, None, None, None, None) == ata.ATA_OK
     assert b"NULL" in lib.ata_last_error_message() or lib.ata_last_error_message() != b""
+
+
+def test_server_argument_checks_without_device():
+    lib = ata.load()
+    h = ctypes.c_void_p()
+    assert lib.ata_server_create(ctypes.byref(h), 0, 1, 4) == ata.ATA_EINVAL       # no budget
+    assert lib.ata_server_create(ctypes.byref(h), 1 << 30, 1, 0) == ata.ATA_EINVAL  # no slots
+    assert lib.ata_server_create(ctypes.byref(h), 1 << 30, 9, 4) == ata.ATA_EINVAL  # dtype
+    t = ctypes.c_uint64()
+    assert lib.ata_submit(None, 1, 1, None, 1, None, ctypes.byref(t)) == ata.ATA_EINVAL
+    assert lib.ata_poll(None, 1, 0) == ata.ATA_EINVAL

@@ -301,111 +301,148 @@ __host__ __device__ constexpr int threads_of() {
 // ---------------------------------------------------------------------------
 // Operand preparation
 
-template <typename TS, int NB>
-__device__ __forceinline__ TS operand_value(const BindSet<NB>& bs, const Term* ts, int t0, int nt, int k, int c) {
-    if (nt == 1) {  // one term: no floating-point addition (sign applied to the bits)
-        const Term& tm = ts[t0];
-        if (k >= tm.rows || c >= tm.cols) return TS(0);
-        const Bind& b = bs.b[tm.inst];
-        const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
-        const TS x = __ldg(base + tm.off + (int64_t)k * tm.ld + c);
-        return tm.neg ? -x : x;
-    }
-    TS v = 0;
-    for (int t = 0; t < nt; ++t) {
-        const Term& tm = ts[t0 + t];
-        if (k < tm.rows && c < tm.cols) {
-            const Bind& b = bs.b[tm.inst];
-            const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
-            const TS x = __ldg(base + tm.off + (int64_t)k * tm.ld + c);
-            v = tm.neg ? v - x : v + x;
-        }
-    }
-    return v;
-}
-
 // Loads a 64 (K) x 64 (column) tile of a leaf operand (a signed sum of
-// terms, zero outside each term's extent) into shared memory, tile[k][c].
-// A thread loads VEC consecutive columns at a time (16 bytes) when the term's
-// rows are 16-byte aligned and all VEC columns are inside it, else element by
-// element; a single term needs no floating-point addition.
+// terms, zero outside each term's extent) into registers: thread t holds the
+// VEC consecutive columns starting at (t % VPR) * VEC of the rows
+// t / VPR + RPP * pass, pass < NPASS.  Every row of one term is loaded before
+// any of them is used, so a thread has NPASS 16-byte loads in flight; a term
+// whose VEC columns are inside it and 16-byte aligned is read with vector
+// loads, else element by element.  A single term needs no floating-point
+// addition (its sign is applied to the bits).
 constexpr int PT = 64;  // prep tile edge
 
+template <typename TS>
+struct TileRegs {
+    static constexpr int VEC = 16 / sizeof(TS);
+    static constexpr int VPR = PT / VEC;     // vectors per tile row
+    static constexpr int RPP = 256 / VPR;    // rows per pass
+    static constexpr int NPASS = PT / RPP;
+    TS v[NPASS][VEC];
+};
+
+template <typename TS>
+__device__ __forceinline__ TS flip_sign(TS x) {
+    if constexpr (sizeof(TS) == 8)
+        return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+    else
+        return __uint_as_float(__float_as_uint(x) ^ 0x80000000u);
+}
+
+template <typename TS, int NB>
+__device__ __forceinline__ void load_operand_regs(const BindSet<NB>& bs, const Term* __restrict__ terms, int t0,
+                                                  int nt, int K, int k0, int c0, TileRegs<TS>& R) {
+    using TR = TileRegs<TS>;
+    constexpr int VEC = TR::VEC, NPASS = TR::NPASS;
+    const int vc = (threadIdx.x % TR::VPR) * VEC;
+    const int r0 = threadIdx.x / TR::VPR;
+#pragma unroll
+    for (int p = 0; p < NPASS; ++p)
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) R.v[p][j] = TS(0);
+    for (int t = 0; t < nt; ++t) {
+        const Term tm = terms[t0 + t];
+        const Bind& b = bs.b[tm.inst];
+        const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
+        const int c = c0 + vc;
+        const TS* colp = base + tm.off + c;
+        const int kmax = min(K, tm.rows);
+        const bool vec_ok = c + VEC <= tm.cols && ((reinterpret_cast<uintptr_t>(colp) & 15) == 0) &&
+                            ((tm.ld * (int64_t)sizeof(TS)) & 15) == 0;
+        TS x[NPASS][VEC];
+        if (vec_ok) {
+#pragma unroll
+            for (int p = 0; p < NPASS; ++p) {
+                const int k = k0 + r0 + p * TR::RPP;
+                uint4 u = make_uint4(0u, 0u, 0u, 0u);
+                if (k < kmax) u = __ldg(reinterpret_cast<const uint4*>(colp + (int64_t)k * tm.ld));
+                *reinterpret_cast<uint4*>(x[p]) = u;
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < NPASS; ++p) {
+                const int k = k0 + r0 + p * TR::RPP;
+#pragma unroll
+                for (int j = 0; j < VEC; ++j)
+                    x[p][j] = (k < kmax && c + j < tm.cols) ? __ldg(colp + (int64_t)k * tm.ld + j) : TS(0);
+            }
+        }
+        if (nt == 1) {
+            if (tm.neg) {
+#pragma unroll
+                for (int p = 0; p < NPASS; ++p)
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) R.v[p][j] = flip_sign(x[p][j]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < NPASS; ++p)
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) R.v[p][j] = x[p][j];
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < NPASS; ++p)
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) R.v[p][j] = tm.neg ? R.v[p][j] - x[p][j] : R.v[p][j] + x[p][j];
+        }
+    }
+}
+
+// The same tile stored to shared memory, tile[k][c].
 template <typename TS, int NB>
 __device__ __forceinline__ void load_operand_tile(const BindSet<NB>& bs, const Term* __restrict__ terms, int t0,
                                                   int nt, int K, int k0, int c0, TS (*tile)[PT + 1]) {
-    constexpr int VEC = 16 / sizeof(TS);
-    constexpr int VPR = PT / VEC;             // vectors per tile row
-    constexpr int RPP = 256 / VPR;            // rows per pass
-    const int vc = (threadIdx.x % VPR) * VEC;  // first column of this thread's vector
-    const int r0 = threadIdx.x / VPR;
+    using TR = TileRegs<TS>;
+    TileRegs<TS> R;
+    load_operand_regs<TS>(bs, terms, t0, nt, K, k0, c0, R);
+    const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
+    const int r0 = threadIdx.x / TR::VPR;
 #pragma unroll
-    for (int pass = 0; pass < PT / RPP; ++pass) {
-        const int kk = r0 + pass * RPP, k = k0 + kk;
-        TS v[VEC];
+    for (int p = 0; p < TR::NPASS; ++p)
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) v[j] = TS(0);
-        if (k < K) {
-            for (int t = 0; t < nt; ++t) {
-                const Term& tm = terms[t0 + t];
-                if (k >= tm.rows) continue;
-                const Bind& b = bs.b[tm.inst];
-                const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
-                const TS* rowp = base + tm.off + (int64_t)k * tm.ld;
-                const int c = c0 + vc;
-                TS x[VEC];
-                if (c + VEC <= tm.cols && ((reinterpret_cast<uintptr_t>(rowp + c) & 15) == 0)) {
-                    const uint4 u = __ldg(reinterpret_cast<const uint4*>(rowp + c));
-                    *reinterpret_cast<uint4*>(x) = u;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) x[j] = (c + j < tm.cols) ? __ldg(rowp + c + j) : TS(0);
-                }
-                if (nt == 1) {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) v[j] = tm.neg ? -x[j] : x[j];
-                } else {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) v[j] = tm.neg ? v[j] - x[j] : v[j] + x[j];
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) tile[kk][vc + j] = v[j];
-    }
+        for (int j = 0; j < TR::VEC; ++j) tile[r0 + p * TR::RPP][vc + j] = R.v[p][j];
 }
 
 // Column maxima of |operand| (sliced modes): atomicMax on the FP64 bit
 // pattern (positive doubles order like their bits; Inf and NaN order above
-// every finite value).  Block: a 64 (K) x 64 (column) tile.
+// every finite value).  Block: a 64 (K) x 64 (column) tile, reduced in
+// registers over a thread's rows, then across the threads of a column.
 template <int NB, typename TS>
 __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ BindSet<NB> bs,
                                                         const LeafProduct* __restrict__ prods,
                                                         const Term* __restrict__ terms,
                                                         const TcProd* __restrict__ tcp,
                                                         const PrepTask* __restrict__ tasks) {
-    __shared__ TS tile[PT][PT + 1];
+    using TR = TileRegs<TS>;
+    constexpr int NRED = 256 / TR::VPR;  // threads sharing a column vector
+    __shared__ unsigned long long red[NRED][PT];
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
-    load_operand_tile<TS>(bs, terms, t0, nt, lp.K, tk.k0, tk.c0, tile);
-    __syncthreads();
+    TileRegs<TS> R;
+    load_operand_regs<TS>(bs, terms, t0, nt, lp.K, tk.k0, tk.c0, R);
     // magnitudes compared as bit patterns (integer operations only)
-    __shared__ unsigned long long red[4][PT];
-    const int col = threadIdx.x % PT, part = threadIdx.x / PT;
-    unsigned long long m = 0;
-    for (int k = part * (PT / 4); k < (part + 1) * (PT / 4); ++k) {
-        unsigned long long b;
-        if constexpr (sizeof(TS) == 8)
-            b = (unsigned long long)__double_as_longlong((double)tile[k][col]) & 0x7FFFFFFFFFFFFFFFull;
-        else
-            b = __float_as_uint((float)tile[k][col]) & 0x7FFFFFFFu;
-        m = b > m ? b : m;
+    const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
+    const int r0 = threadIdx.x / TR::VPR;
+#pragma unroll
+    for (int j = 0; j < TR::VEC; ++j) {
+        unsigned long long m = 0;
+#pragma unroll
+        for (int p = 0; p < TR::NPASS; ++p) {
+            unsigned long long b;
+            if constexpr (sizeof(TS) == 8)
+                b = (unsigned long long)__double_as_longlong((double)R.v[p][j]) & 0x7FFFFFFFFFFFFFFFull;
+            else
+                b = __float_as_uint((float)R.v[p][j]) & 0x7FFFFFFFu;
+            m = b > m ? b : m;
+        }
+        red[r0][vc + j] = m;
     }
-    red[part][col] = m;
     __syncthreads();
     if (threadIdx.x < PT) {
-        for (int i = 1; i < 4; ++i) m = red[i][col] > m ? red[i][col] : m;
+        const int col = threadIdx.x;
+        unsigned long long m = red[0][col];
+#pragma unroll
+        for (int i = 1; i < NRED; ++i) m = red[i][col] > m ? red[i][col] : m;
         if (m != 0) {
             if constexpr (sizeof(TS) == 4) m = (unsigned long long)__double_as_longlong((double)__uint_as_float((unsigned)m));
             unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);

@@ -101,6 +101,13 @@ typedef struct {
     int64_t classical_mults;    /* m * n (n + 1) / 2                        */
     int64_t adds;               /* scalar additions of Strassen sums/combines*/
     int64_t workspace_bytes;    /* device workspace the plan allocates      */
+    int32_t leaf_tile_rows;     /* output tile of the leaf kernel: rows ... */
+    int32_t leaf_tile_cols;     /* ... and columns.  Tensor-core leaves use
+                                   256 x 128 tiles (two SMs per tile, a CTA
+                                   pair) when every leaf is padded to them;
+                                   ata_plan_query reports the planned shape,
+                                   ata_plan_get_info the one that runs on
+                                   the plan's device                        */
 } ata_plan_info;
 
 /* Status text ("ATA_OK", ...).  Never NULL. */

@@ -43,7 +43,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_leaf_products", ctypes.c_int32), ("n_leaf_tiles", ctypes.c_int32),
                 ("n_sum_tasks", ctypes.c_int32), ("n_combine_tasks", ctypes.c_int32),
                 ("n_launches", ctypes.c_int32), ("mults", ctypes.c_int64), ("classical_mults", ctypes.c_int64),
-                ("adds", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+                ("adds", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("leaf_tile_rows", ctypes.c_int32), ("leaf_tile_cols", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -11,8 +11,9 @@
 // Part products are exact in FP32.  The tensor core accumulates in FP32
 // with truncation, so an accumulator that runs over a long K drifts by a
 // relative ~2^-23 per addition.  Orders whose share of the result is large
-// are therefore accumulated per K chunk of 128 in their own accumulator, in
-// which every partial sum is an integer below 2^24 units (exact), and drained
+// are therefore accumulated per K chunk of 256 in their own accumulator, in
+// which every partial sum is an integer of at most 2^24 units (a leading-digit
+// product is at most 2^16 units, so 256 of them stay exact), and drained
 // into float-float (hi, lo) sums by the epilogue after each chunk: orders 0-1
 // for bf16x3, 0-2 for ozaki.  The remaining orders (2 for bf16x3: ~2^-16 of
 // the result, accumulated over the whole K; 3-5 for ozaki, drained per chunk)
@@ -40,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -78,15 +80,28 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// CG == 2 waits acquire at cluster scope: the barrier may complete through
+// arrivals of the other CTA of the pair.
+template <int CG = 1>
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
+    if constexpr (CG == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    }
     return ok != 0;
 }
 
@@ -94,11 +109,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // (after recording `code` in *status unless another role already did) when
 // the wait gives up: on a timeout, or when *status shows that another role
 // gave up first.
+template <int CG = 1>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait<CG>(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait<CG>(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*reinterpret_cast<volatile int*>(status) != 0) return false;
             if (globaltimer() - t0 > kTimeoutNs) {
@@ -109,46 +125,139 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint32_t bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
-        "[%2];" ::"r"(dst),
-        "l"(tmap), "r"(bar), "r"(x), "r"(y)
-        : "memory");
+// Bounded wait that records nothing (teardown: copies or MMAs in flight).
+template <int CG = 1>
+__device__ __forceinline__ void mbar_wait_quiet(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait<CG>(bar, parity) && globaltimer() - t0 < kTimeoutNs) {
+    }
 }
 
+// Cluster helpers (the CTA-pair kernel runs in clusters of two CTAs; its
+// even CTA -- rank 0 -- issues every MMA of the pair).
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Address, in the cluster window, of the same shared-memory offset in CTA `rank`.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+// Every thread of both CTAs: release what this thread wrote, wait for all.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// Arrive on an mbarrier given by its cluster-window address (any CTA of the cluster).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+// TMA 2D tile load into this CTA's shared memory.  CG == 1: completion on
+// `bar` of this CTA.  CG == 2: `bar` is a cluster-window address and may be
+// the pair's even CTA's barrier, which counts both CTAs' bytes.
+template <int CG>
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint32_t bar, int x, int y) {
+    if constexpr (CG == 1) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+            "[%2];" ::"r"(dst),
+            "l"(tmap), "r"(bar), "r"(x), "r"(y)
+            : "memory");
+    } else {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+            "l"(tmap), "r"(bar), "r"(x), "r"(y)
+            : "memory");
+    }
+}
+
+// TMEM allocation: CG == 2 allocates the same columns in both CTAs of the
+// pair; one warp of each CTA executes it (and the matching dealloc).
+template <int CG>
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+    if constexpr (CG == 1)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+    else
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
 }
+template <int CG>
 __device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (CG == 1)
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    else
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
 }
+template <int CG>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+    if constexpr (CG == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+    else
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <int MODE>
+// D (TMEM) [+]= A (smem) x B (smem).  CG == 2: M = 256 over the pair, A's
+// rows 0-127 and B's first N/2 rows in the even CTA, the rest at the same
+// shared-memory offsets in the odd CTA; each CTA's TMEM receives its 128 rows.
+template <int MODE, int CG>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    if constexpr (MODE == MODE_TF32) {
+    if constexpr (MODE == MODE_TF32 && CG == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
             : "memory");
-    } else {
+    } else if constexpr (MODE == MODE_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else if constexpr (CG == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
             : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
     }
 }
 
+// Arrive on `bar` once every MMA issued so far by this thread has completed;
+// CG == 2 arrives on the barrier at the same offset in both CTAs of the pair.
+template <int CG>
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    if constexpr (CG == 1) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+    } else {
+        const uint16_t mask = 3;
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                bar),
+            "h"(mask)
+            : "memory");
+    }
 }
 
 // 32 lanes x 32 bit, 16 consecutive columns per thread.
@@ -246,57 +355,59 @@ struct Geo;
 // accumulator, over the whole K (F_FINAL) or drained per chunk.
 template <>
 struct Geo<MODE_BF16X3> {
-    static constexpr int PARTS = 3, ELEM = 2, KBLK = 32, ROWB = 64, KSTEP = 16, NSTAGE = 3;
+    static constexpr int PARTS = 3, ELEM = 2, KBLK = 32, ROWB = 64, KSTEP = 16, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 4, SBO = 512;  // 64B swizzle
     static constexpr int KC = 256, ND = 2, DMAX = 2, DBUF = 2, FMIN = 1, FMAX = 0;  // no F group
     static constexpr bool F_FINAL = false, SLICED = true;
     static constexpr int EPI_WARPS = 16;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 0;
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    static constexpr uint32_t IDESC_KIND = (1u << 4) | (1u << 7) | (1u << 10);  // F32 D, bf16 A and B
 };
 
 template <>
 struct Geo<MODE_TF32> {
-    static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6;
+    static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6, NSTAGE2 = 8;
     static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
     static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0;
     static constexpr bool F_FINAL = true, SLICED = false;
     static constexpr int EPI_WARPS = 8;
     static constexpr uint32_t TMEM_COLS = 128, F_COL = 0;
-    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    static constexpr uint32_t IDESC_KIND = (1u << 4) | (2u << 7) | (2u << 10);  // F32 D, tf32 A and B
 };
 
 template <>
 struct Geo<MODE_OZAKI> {
-    static constexpr int PARTS = 6, ELEM = 2, KBLK = 16, ROWB = 32, KSTEP = 16, NSTAGE = 3;
+    static constexpr int PARTS = 6, ELEM = 2, KBLK = 16, ROWB = 32, KSTEP = 16, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 6, SBO = 256;  // 32B swizzle
-    static constexpr int KC = 128, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5;
+    static constexpr int KC = 256, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5;
     static constexpr bool F_FINAL = false, SLICED = true;
     static constexpr int EPI_WARPS = 16;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 384;
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    static constexpr uint32_t IDESC_KIND = (1u << 4) | (1u << 7) | (1u << 10);  // F32 D, bf16 A and B
 };
 
-template <int MODE>
-__host__ __device__ constexpr int tile_bytes() {
-    return 128 * Geo<MODE>::ROWB;
-}
-template <int MODE>
-__host__ __device__ constexpr int stage_bytes() {
-    return 2 * Geo<MODE>::PARTS * tile_bytes<MODE>();
-}
-template <int MODE>
-__host__ __device__ constexpr int lo_smem_bytes() {
-    return Geo<MODE>::ND > 0 ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
-}
-template <int MODE>
-__host__ __device__ constexpr int smem_bytes() {
-    return Geo<MODE>::NSTAGE * stage_bytes<MODE>() + lo_smem_bytes<MODE>() + 1024 /*align*/ + 256 /*barriers*/;
-}
-template <int MODE>
-__host__ __device__ constexpr int threads_of() {
-    return 32 * (2 + Geo<MODE>::EPI_WARPS);
-}
+// Per-CTA shapes of the leaf GEMM.  CG == 1: one CTA computes a 128 x 128
+// tile (M = N = 128).  CG == 2: a pair of CTAs computes a 256 x 128 tile
+// (M = 256, N = 128); each CTA holds 128 rows of the X parts, 64 rows of the
+// Y parts, and the 128 x 128 accumulator rows of its half.  Halving the Y
+// rows each CTA stages halves the B-operand shared-memory reads per MMA.
+template <int MODE, int CG>
+struct Shape {
+    using G = Geo<MODE>;
+    static constexpr int XROWS = 128, YROWS = 128 / CG;
+    static constexpr int X_BYTES = XROWS * G::ROWB, Y_BYTES = YROWS * G::ROWB;
+    static constexpr int STAGE = G::PARTS * (X_BYTES + Y_BYTES);
+    static constexpr int LO = G::ND > 0 ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
+    static constexpr int NSTAGE = CG == 1 ? G::NSTAGE : G::NSTAGE2;
+    // CG == 2 keeps at least Y_BYTES of allocation after the last stage, so
+    // that the operand reads of its last Y part stay inside this CTA's
+    // shared memory whatever the B rows the pair MMA takes per CTA
+    static constexpr int TAIL = CG == 2 && LO < Y_BYTES ? Y_BYTES : 0;
+    static constexpr int SMEM = NSTAGE * STAGE + LO + 1024 /*align*/ + 256 /*barriers*/ + TAIL;
+    static constexpr uint32_t IDESC = G::IDESC_KIND | ((128u >> 3) << 17) | ((128u * CG >> 4) << 24);
+    static constexpr int THREADS = 32 * (2 + G::EPI_WARPS);
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+};
 
 // ---------------------------------------------------------------------------
 // Operand preparation
@@ -570,13 +681,22 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
 
 // ---------------------------------------------------------------------------
 // Persistent tcgen05 GEMM over leaf tiles
+//
+// CG == 1: one CTA per SM, each CTA takes tiles blockIdx.x, + gridDim.x, ...
+// CG == 2: clusters of two CTAs (a pair on two SMs); each pair takes tiles
+// clusterid, + nclusterid, ...  Both CTAs run the TMA producer for their own
+// halves (completing on the even CTA's full barrier, which expects the bytes
+// of both) and the epilogue for their own 128 rows; the even CTA's MMA warp
+// issues the MMAs, whose commits arrive on the barriers of both CTAs.  The
+// even CTA's dempty / fempty barriers count the epilogue warps of both.
 
-template <int NB, int MODE>
-__global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __grid_constant__ BindSet<NB> bs,
-                                                                       const TcProd* __restrict__ tcp,
-                                                                       const LeafTile* __restrict__ tiles,
-                                                                       int ntiles, int* __restrict__ status) {
+template <int NB, int MODE, int CG>
+__global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ BindSet<NB> bs, const TcProd* __restrict__ tcp,
+                   const LeafTile* __restrict__ tiles, int ntiles, int* __restrict__ status) {
     using G = Geo<MODE>;
+    using SH = Shape<MODE, CG>;
+    constexpr int NSTAGE = SH::NSTAGE;
     constexpr int NCOL = 128 / (G::EPI_WARPS / 4);  // columns per epilogue thread
     constexpr int NG = NCOL / 16;                   // 16-column groups per thread
     constexpr int kbpc = G::KC / G::KBLK > 0 ? G::KC / G::KBLK : 1;
@@ -584,86 +704,101 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
     constexpr int NKS = G::KBLK / G::KSTEP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* lo_s = reinterpret_cast<float*>(smem + G::NSTAGE * stage_bytes<MODE>());  // [col][row]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSTAGE * stage_bytes<MODE>() + lo_smem_bytes<MODE>());
+    float* lo_s = reinterpret_cast<float*>(smem + NSTAGE * SH::STAGE);  // [col][row]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * SH::STAGE + SH::LO);
     // barriers: full[NSTAGE] empty[NSTAGE] dfull[DBUF] dempty[DBUF] ffull fempty done ; tmem slot
-    const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * G::NSTAGE;
-    const uint32_t b_dfull = b_empty + 8 * G::NSTAGE, b_dempty = b_dfull + 8 * G::DBUF;
+    const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * NSTAGE;
+    const uint32_t b_dfull = b_empty + 8 * NSTAGE, b_dempty = b_dfull + 8 * G::DBUF;
     const uint32_t b_ffull = b_dempty + 8 * G::DBUF, b_fempty = b_ffull + 8, b_done = b_fempty + 8;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * G::NSTAGE + 2 * G::DBUF + 3);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSTAGE + 2 * G::DBUF + 3);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = CG == 1 ? 0u : cluster_rank();
+    const int tile0 = CG == 1 ? (int)blockIdx.x : (int)cluster_index();
+    const int tstep = CG == 1 ? (int)gridDim.x : (int)cluster_count();
     if (threadIdx.x == 0) {
-        for (int s = 0; s < G::NSTAGE; ++s) {
+        for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(b_full + 8 * s, 1);
             mbar_init(b_empty + 8 * s, 1);
         }
         for (int s = 0; s < G::DBUF; ++s) {
             mbar_init(b_dfull + 8 * s, 1);
-            mbar_init(b_dempty + 8 * s, G::EPI_WARPS);
+            mbar_init(b_dempty + 8 * s, G::EPI_WARPS * CG);
         }
         mbar_init(b_ffull, 1);
-        mbar_init(b_fempty, G::EPI_WARPS);
+        mbar_init(b_fempty, G::EPI_WARPS * CG);
         mbar_init(b_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), G::TMEM_COLS);
-        tmem_relinquish();
+        tmem_alloc<CG>(smem_u32(tmem_slot), G::TMEM_COLS);
+        tmem_relinquish<CG>();
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (CG == 1)
+        __syncthreads();
+    else
+        cluster_sync_all();  // both CTAs' barriers initialised and TMEM allocated
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t smem_base = smem_u32(smem);
+    // barriers that the epilogue warps of both CTAs arrive on: the even CTA's
+    const uint32_t b_dempty_c = CG == 1 ? b_dempty : map_to_rank(b_dempty, 0);
+    const uint32_t b_fempty_c = CG == 1 ? b_fempty : map_to_rank(b_fempty, 0);
+    const uint32_t b_full_c = CG == 1 ? b_full : map_to_rank(b_full, 0);
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = tile0; t < ntiles && ok; t += tstep) {
                 const LeafTile lt = tiles[t];
                 const TcProd* pr = tcp + lt.prod;
                 const int nkb = pr->K_pad / G::KBLK;
-                const int ya = lt.ti * 128, yb = lt.tj * 128;
+                const int ya = lt.ti * (128 * CG) + (int)rank * SH::XROWS;
+                const int yb = lt.tj * 128 + (int)rank * SH::YROWS;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const uint32_t s = it % G::NSTAGE, ph = (it / G::NSTAGE) & 1;
-                    if (!mbar_wait(b_empty + 8 * s, ph ^ 1, status, ERR_TIMEOUT_PRODUCER)) {
+                    const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
+                    if (!mbar_wait<CG>(b_empty + 8 * s, ph ^ 1, status, ERR_TIMEOUT_PRODUCER)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(b_full + 8 * s, stage_bytes<MODE>());
-                    const uint32_t st = smem_base + s * stage_bytes<MODE>();
+                    if (rank == 0) mbar_expect_tx(b_full + 8 * s, CG * SH::STAGE);
+                    const uint32_t st = smem_base + s * SH::STAGE;
 #pragma unroll
                     for (int q = 0; q < G::PARTS; ++q) {
-                        tma_load_2d(st + q * tile_bytes<MODE>(), &pr->tmx, b_full + 8 * s, kb * G::KBLK,
-                                    q * pr->p_pad + ya);
-                        tma_load_2d(st + (G::PARTS + q) * tile_bytes<MODE>(), &pr->tmy, b_full + 8 * s,
-                                    kb * G::KBLK, q * pr->r_pad + yb);
+                        tma_load_2d<CG>(st + q * SH::X_BYTES, &pr->tmx, b_full_c + 8 * s, kb * G::KBLK,
+                                        q * pr->p_pad + ya);
+                        tma_load_2d<CG>(st + G::PARTS * SH::X_BYTES + q * SH::Y_BYTES, &pr->tmy, b_full_c + 8 * s,
+                                        kb * G::KBLK, q * pr->r_pad + yb);
                     }
                 }
             }
-            // copies still in flight land before the CTA may exit (bounded)
-            const uint32_t n_in_flight = it < (uint32_t)G::NSTAGE ? it : (uint32_t)G::NSTAGE;
+            // copies still in flight land before the CTA may exit (bounded): the
+            // even CTA sees its full barriers complete; the odd CTA, whose copies
+            // complete on the even CTA's barriers, waits until the MMAs that read
+            // them have released the stage
+            const uint32_t n_in_flight = it < (uint32_t)NSTAGE ? it : (uint32_t)NSTAGE;
             for (uint32_t j = 0; j < n_in_flight; ++j) {
                 const uint32_t i2 = it - 1 - j;
-                const uint32_t s = i2 % G::NSTAGE, ph = (i2 / G::NSTAGE) & 1;
-                const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(b_full + 8 * s, ph) && globaltimer() - t0 < kTimeoutNs) {
-                }
+                const uint32_t s = i2 % NSTAGE, ph = (i2 / NSTAGE) & 1;
+                if (rank == 0)
+                    mbar_wait_quiet<CG>(b_full + 8 * s, ph);
+                else
+                    mbar_wait_quiet<CG>(b_empty + 8 * s, ph);
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {
             uint32_t it = 0, chunk = 0, tcount = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+            for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
                 const LeafTile lt = tiles[t];
                 const int nkb = tcp[lt.prod].K_pad / G::KBLK;
                 if constexpr (G::F_FINAL) {
-                    if (!mbar_wait(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
+                    if (!mbar_wait<CG>(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
                         ok = false;
                         break;
                     }
@@ -673,24 +808,25 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                     const bool last_in_chunk = (kb % kbpc) == kbpc - 1 || kb == nkb - 1;
                     const uint32_t buf = chunk % G::DBUF;
                     if (G::ND > 0 && first_in_chunk) {
-                        if (!mbar_wait(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
+                        if (!mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
+                                           ERR_TIMEOUT_MMA)) {
                             ok = false;
                             break;
                         }
                     }
-                    const uint32_t s = it % G::NSTAGE, ph = (it / G::NSTAGE) & 1;
-                    if (!mbar_wait(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA)) {
+                    const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
+                    if (!mbar_wait<CG>(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = smem_base + s * stage_bytes<MODE>();
+                    const uint32_t st = smem_base + s * SH::STAGE;
                     auto desc_a = [&](int q, int ks) {
-                        return make_desc(st + q * tile_bytes<MODE>() + ks * G::KSTEP * G::ELEM, G::SBO, G::SWZ);
+                        return make_desc(st + q * SH::X_BYTES + ks * G::KSTEP * G::ELEM, G::SBO, G::SWZ);
                     };
                     auto desc_b = [&](int q, int ks) {
-                        return make_desc(st + (G::PARTS + q) * tile_bytes<MODE>() + ks * G::KSTEP * G::ELEM, G::SBO,
-                                         G::SWZ);
+                        return make_desc(st + G::PARTS * SH::X_BYTES + q * SH::Y_BYTES + ks * G::KSTEP * G::ELEM,
+                                         G::SBO, G::SWZ);
                     };
                     if constexpr (G::ND > 0) {
                         // D group: order d into accumulator min(d, ND-1); each accumulator is
@@ -705,16 +841,17 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                                 if (a >= G::PARTS || ord - a >= G::PARTS) continue;
 #pragma unroll
                                 for (int ks = 0; ks < NKS; ++ks) {
-                                    umma<MODE>(d, desc_a(a, ks), desc_b(ord - a, ks), G::IDESC, fresh[acc] ? 0u : 1u);
+                                    umma<MODE, CG>(d, desc_a(a, ks), desc_b(ord - a, ks), SH::IDESC,
+                                                   fresh[acc] ? 0u : 1u);
                                     fresh[acc] = false;
                                 }
                             }
                         }
-                        if (last_in_chunk) umma_commit(b_dfull + 8 * buf);
+                        if (last_in_chunk) umma_commit<CG>(b_dfull + 8 * buf);
                     }
                     if constexpr (HAS_F) {
                         if (!G::F_FINAL && first_in_chunk) {
-                            if (!mbar_wait(b_fempty, (chunk & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
+                            if (!mbar_wait<CG>(b_fempty, (chunk & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
                                 ok = false;
                                 break;
                             }
@@ -727,24 +864,25 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                                 if (a >= G::PARTS || ord - a >= G::PARTS) continue;
 #pragma unroll
                                 for (int ks = 0; ks < NKS; ++ks) {
-                                    umma<MODE>(tmem + G::F_COL, desc_a(a, ks), desc_b(ord - a, ks), G::IDESC,
-                                               first ? 0u : 1u);
+                                    umma<MODE, CG>(tmem + G::F_COL, desc_a(a, ks), desc_b(ord - a, ks), SH::IDESC,
+                                                   first ? 0u : 1u);
                                     first = false;
                                 }
                             }
-                        if (!G::F_FINAL && last_in_chunk) umma_commit(b_ffull);
+                        if (!G::F_FINAL && last_in_chunk) umma_commit<CG>(b_ffull);
                     }
-                    umma_commit(b_empty + 8 * s);  // stage reusable once these MMAs finish
+                    umma_commit<CG>(b_empty + 8 * s);  // stage reusable once these MMAs finish
                     if (last_in_chunk) ++chunk;
                 }
                 if (!ok) break;
-                if constexpr (G::F_FINAL) umma_commit(b_ffull);
+                if constexpr (G::F_FINAL) umma_commit<CG>(b_ffull);
             }
             // every issued MMA completes before TMEM is released (bounded)
-            umma_commit(b_done);
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(b_done, 0) && globaltimer() - t0 < kTimeoutNs) {
-            }
+            umma_commit<CG>(b_done);
+            mbar_wait_quiet<CG>(b_done, 0);
+        } else if (lane == 0) {
+            // odd CTA of a pair: the even CTA's final commit arrives here too
+            mbar_wait_quiet<CG>(b_done, 0);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -757,7 +895,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
         const int row = 32 * q + lane;
         uint32_t chunk = 0, tcount = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+        for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
             const LeafTile lt = tiles[t];
             const TcProd* pr = tcp + lt.prod;
             const int nkb = pr->K_pad / G::KBLK;
@@ -768,7 +906,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
             if constexpr (G::ND > 0) {
                 for (int ci = 0; ci < nchunks; ++ci, ++chunk) {
                     const uint32_t buf = chunk % G::DBUF;
-                    if (!mbar_wait(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                    if (!mbar_wait<CG>(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE)) {
                         ok = false;
                         break;
                     }
@@ -804,9 +942,14 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(b_dempty + 8 * buf);
+                    if (lane == 0) {
+                        if constexpr (CG == 1)
+                            mbar_arrive(b_dempty + 8 * buf);
+                        else
+                            mbar_arrive_cluster(b_dempty_c + 8 * buf);
+                    }
                     if constexpr (HAS_F && !G::F_FINAL) {
-                        if (!mbar_wait(b_ffull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                        if (!mbar_wait<CG>(b_ffull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
                             ok = false;
                             break;
                         }
@@ -821,13 +964,18 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                         }
                         tc_fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(b_fempty);
+                        if (lane == 0) {
+                            if constexpr (CG == 1)
+                                mbar_arrive(b_fempty);
+                            else
+                                mbar_arrive_cluster(b_fempty_c);
+                        }
                     }
                 }
                 if (!ok) break;
             }
             if constexpr (G::F_FINAL) {
-                if (!mbar_wait(b_ffull, tcount & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                if (!mbar_wait<CG>(b_ffull, tcount & 1, status, ERR_TIMEOUT_EPILOGUE)) {
                     ok = false;
                     break;
                 }
@@ -835,7 +983,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
             }
             // FP64 tile: row i of this thread, NCOL columns in groups of 16
             const Bind& bind = bs.b[pr->inst];
-            const int i = lt.ti * 128 + row;
+            const int i = lt.ti * (128 * CG) + (int)rank * 128 + row;
             const int j0 = lt.tj * 128 + cq * NCOL;
             const bool row_ok = i < pr->out_rows;
             int Ei = 0;
@@ -886,17 +1034,27 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1) tc_gemm_kernel(const __
                 // accumulator read: TMEM may be refilled by the next tile
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(b_fempty);
+                if (lane == 0) {
+                    if constexpr (CG == 1)
+                        mbar_arrive(b_fempty);
+                    else
+                        mbar_arrive_cluster(b_fempty_c);
+                }
             }
         }
     }
 
-    // teardown: every role has stopped issuing and every MMA has completed
+    // teardown: every role has stopped issuing and every MMA has completed;
+    // in a pair neither CTA leaves while the other may still reach its
+    // shared memory (remote arrivals, MMA operand reads)
     tc_fence_before();
-    __syncthreads();
+    if constexpr (CG == 1)
+        __syncthreads();
+    else
+        cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, G::TMEM_COLS);
+        tmem_dealloc<CG>(tmem, G::TMEM_COLS);
     }
 }
 
@@ -917,14 +1075,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
+// TMA map of the stacked parts of one operand: rows (parts x rows_pad) of
+// K_pad elements, a box of KBLK x box_rows, swizzled to the UMMA K-major layout.
 template <int MODE>
-bool encode_parts(CUtensorMap* map, char* base, int parts, int rows_pad, int K_pad) {
+bool encode_parts(CUtensorMap* map, char* base, int parts, int rows_pad, int K_pad, int box_rows) {
     using G = Geo<MODE>;
     auto enc = get_encode();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)parts * rows_pad};
     const cuuint64_t strides[1] = {(cuuint64_t)K_pad * G::ELEM};
-    const cuuint32_t box[2] = {(cuuint32_t)G::KBLK, 128};
+    const cuuint32_t box[2] = {(cuuint32_t)G::KBLK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt =
         G::ELEM == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -935,16 +1095,26 @@ bool encode_parts(CUtensorMap* map, char* base, int parts, int rows_pad, int K_p
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_for(LeafKind k, CUtensorMap* map, char* base, int rows_pad, int K_pad) {
+bool encode_for(LeafKind k, CUtensorMap* map, char* base, int rows_pad, int K_pad, int box_rows) {
     switch (k) {
-        case LEAF_BF16X3: return encode_parts<MODE_BF16X3>(map, base, 3, rows_pad, K_pad);
-        case LEAF_TF32: return encode_parts<MODE_TF32>(map, base, 1, rows_pad, K_pad);
-        case LEAF_OZAKI: return encode_parts<MODE_OZAKI>(map, base, 6, rows_pad, K_pad);
+        case LEAF_BF16X3: return encode_parts<MODE_BF16X3>(map, base, 3, rows_pad, K_pad, box_rows);
+        case LEAF_TF32: return encode_parts<MODE_TF32>(map, base, 1, rows_pad, K_pad, box_rows);
+        case LEAF_OZAKI: return encode_parts<MODE_OZAKI>(map, base, 6, rows_pad, K_pad, box_rows);
         default: return false;
     }
 }
 
-int g_sms = 1;  // SM count of the device (set before any capture)
+int g_sms = 1;                    // SM count of the device (set before any capture)
+int g_pair_clusters[4] = {0, 0, 0, 0};  // co-resident CTA pairs per mode (0: pair kernel unavailable)
+
+cudaLaunchAttribute pair_cluster_attr() {
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 2;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = 1;
+    return a;
+}
 
 template <int NB, int MODE>
 cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s, cudaEvent_t before_gemm) {
@@ -959,8 +1129,25 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
         cudaError_t e = cudaEventRecordWithFlags(before_gemm, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
+    if constexpr (NB == 1) {
+        if (t.tc_pair) {
+            using SH = Shape<MODE, 2>;
+            if (g_pair_clusters[MODE] < 1) return cudaErrorInvalidConfiguration;
+            const int nclus = std::max(1, std::min(t.ntiles, g_pair_clusters[MODE]));
+            cudaLaunchAttribute at[1] = {pair_cluster_attr()};
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2 * nclus);
+            cfg.blockDim = dim3(SH::THREADS);
+            cfg.dynamicSmemBytes = SH::SMEM;
+            cfg.stream = s;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, MODE, 2>, bs, t.tcp, t.tiles, t.ntiles, t.status);
+        }
+    }
+    using SH = Shape<MODE, 1>;
     const int grid = std::max(1, std::min(t.ntiles, g_sms));
-    tc_gemm_kernel<NB, MODE><<<grid, threads_of<MODE>(), smem_bytes<MODE>(), s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status);
+    tc_gemm_kernel<NB, MODE, 1><<<grid, SH::THREADS, SH::SMEM, s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status);
     return cudaGetLastError();
 }
 
@@ -974,10 +1161,34 @@ cudaError_t launch_kind(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
     }
 }
 
-template <int NB, int MODE>
+template <int NB, int MODE, int CG>
 cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(tc_gemm_kernel<NB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_bytes<MODE>());
+    return cudaFuncSetAttribute(tc_gemm_kernel<NB, MODE, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Shape<MODE, CG>::SMEM);
+}
+
+// How many CTA pairs of the MODE kernel fit on the device at once (0 when the
+// pair kernel cannot be launched here).
+template <int MODE>
+int pair_clusters() {
+    using SH = Shape<MODE, 2>;
+    if (set_smem_attr<1, MODE, 2>() != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchAttribute at[1] = {pair_cluster_attr()};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * std::max(1, g_sms / 2));
+    cfg.blockDim = dim3(SH::THREADS);
+    cfg.dynamicSmemBytes = SH::SMEM;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<1, MODE, 2>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::max(0, n);
 }
 
 }  // namespace
@@ -990,12 +1201,12 @@ ata_status tc_prepare_device() {
     static cudaError_t err = cudaErrorNotReady;
     static std::once_flag once;
     std::call_once(once, [] {
-        err = set_smem_attr<1, MODE_BF16X3>();
-        if (err == cudaSuccess) err = set_smem_attr<1, MODE_TF32>();
-        if (err == cudaSuccess) err = set_smem_attr<1, MODE_OZAKI>();
-        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_BF16X3>();
-        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_TF32>();
-        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_OZAKI>();
+        err = set_smem_attr<1, MODE_BF16X3, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<1, MODE_TF32, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<1, MODE_OZAKI, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_BF16X3, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_TF32, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_OZAKI, 1>();
         if (err == cudaSuccess && !get_encode()) err = cudaErrorNotSupported;
         if (err == cudaSuccess) {
             int dev = 0;
@@ -1003,9 +1214,20 @@ ata_status tc_prepare_device() {
             if (err == cudaSuccess) err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
             if (g_sms <= 0) g_sms = 1;
         }
+        if (err == cudaSuccess && !std::getenv("ATA_NO_CTA_PAIR")) {
+            g_pair_clusters[MODE_BF16X3] = pair_clusters<MODE_BF16X3>();
+            g_pair_clusters[MODE_TF32] = pair_clusters<MODE_TF32>();
+            g_pair_clusters[MODE_OZAKI] = pair_clusters<MODE_OZAKI>();
+        }
     });
     if (err != cudaSuccess) return cuda_fail(err, "tensor-core leaf set-up");
     return ATA_OK;
+}
+
+int tc_rows_for(const Plan& P) {
+    if (P.leaf == LEAF_F64 || P.tc_tile_rows != kTcPairRows) return kTcTile;
+    if (tc_prepare_device() != ATA_OK) return kTcTile;
+    return g_pair_clusters[P.leaf] > 0 ? kTcPairRows : kTcTile;
 }
 
 ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d) {
@@ -1020,8 +1242,10 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         TcProd& t = tp[i];
         std::memset(&t, 0, sizeof(t));
         char* W = ws[lp.inst];
-        if (!encode_for(h.leaf, &t.tmx, W + lp.tc_x_off, lp.p_pad, lp.K_pad) ||
-            !encode_for(h.leaf, &t.tmy, W + lp.tc_y_off, lp.r_pad, lp.K_pad))
+        // CTA pairs: each CTA stages 128 X rows and half of the 128 Y rows
+        const int ybox = h.tile_rows == kTcPairRows ? kTcTile / 2 : kTcTile;
+        if (!encode_for(h.leaf, &t.tmx, W + lp.tc_x_off, lp.p_pad, lp.K_pad, kTcTile) ||
+            !encode_for(h.leaf, &t.tmy, W + lp.tc_y_off, lp.r_pad, lp.K_pad, ybox))
             return fail(ATA_ECUDA, "cuTensorMapEncodeTiled failed for a leaf operand");
         t.p_pad = lp.p_pad;
         t.r_pad = lp.r_pad;

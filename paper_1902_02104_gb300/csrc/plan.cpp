@@ -142,8 +142,11 @@ void emit_leaf(Ctx& c, const std::vector<Term>& X, const std::vector<Term>& Y, i
     if (P.leaf != LEAF_F64) {
         // split parts of both operands, K-major, zero padded to whole tiles
         const TcGeom g = tc_geom(P.leaf);
-        lp.p_pad = (int32_t)((p + kTcTile - 1) / kTcTile * kTcTile);
-        lp.r_pad = (int32_t)((r + kTcTile - 1) / kTcTile * kTcTile);
+        // X rows of a leaf above one tile are padded to whole CTA-pair tiles
+        // (256 rows); a SYRK leaf reads the same buffer as Y
+        const int64_t xr = p > kTcTile ? kTcPairRows : kTcTile;
+        lp.p_pad = (int32_t)((p + xr - 1) / xr * xr);
+        lp.r_pad = syrk ? lp.p_pad : (int32_t)((r + kTcTile - 1) / kTcTile * kTcTile);
         lp.K_pad = (int32_t)std::max<int64_t>((K + g.k_align - 1) / g.k_align * g.k_align, g.k_align);
         lp.tc_x_off = c.alloc((int64_t)g.parts * lp.p_pad * lp.K_pad * g.elem);
         lp.tc_y_off = syrk ? lp.tc_x_off : c.alloc((int64_t)g.parts * lp.r_pad * lp.K_pad * g.elem);
@@ -334,8 +337,10 @@ TcGeom tc_geom(LeafKind k) {
 int64_t leaf_tiles(const LeafProduct& p, int tm, int tn) {
     const int64_t a = (p.out_rows + tm - 1) / tm, b = (p.out_cols + tn - 1) / tn;
     if (p.out_kind == OUT_SYRK) {
-        // upper tiles (tile column >= tile row); tm == tn
-        return a * (a + 1) / 2;
+        // tiles that hold an upper entry: tile column tj from (ti * tm) / tn on
+        int64_t cnt = 0;
+        for (int64_t ti = 0; ti < a; ++ti) cnt += std::max<int64_t>(0, b - ti * tm / tn);
+        return cnt;
     }
     return a * b;
 }
@@ -373,6 +378,18 @@ bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::st
     c.opt = &opt;
     if (n > 0) recurse_columns(c, 0, n, 0);
     P.ws_bytes = c.ws;
+    if (P.leaf != LEAF_F64) {
+        // CTA-pair tiles when every X operand is padded to them and they add
+        // at most 1/8 to the tile area of 128-row tiles
+        bool all = !P.products.empty();
+        double a1 = 0, a2 = 0;
+        for (const LeafProduct& lp : P.products) {
+            all = all && lp.p_pad % kTcPairRows == 0;
+            a1 += (double)leaf_tiles(lp, kTcTile, kTcTile) * kTcTile * kTcTile;
+            a2 += (double)leaf_tiles(lp, kTcPairRows, kTcTile) * kTcPairRows * kTcTile;
+        }
+        P.tc_tile_rows = all && a2 <= 1.125 * a1 ? kTcPairRows : kTcTile;
+    }
     return true;
 }
 

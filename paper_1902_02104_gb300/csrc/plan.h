@@ -120,6 +120,8 @@ struct Plan {
     std::vector<std::vector<SplitTask>> split_levels;    // [l] builds level l+1 operands
     std::vector<std::vector<CombineTask>> combine_levels; // [l] children at level l+1 -> level l
     int64_t ws_bytes = 0;
+    int tc_tile_rows = 0;     // tensor-core leaves: 256 when every X operand is padded to
+                              // whole 256-row tiles (the CTA-pair kernel applies), else 128
     PlanStats stats;
 };
 
@@ -130,7 +132,8 @@ struct TcGeom {
     int k_align;     // K padding of part buffers (elements)
 };
 TcGeom tc_geom(LeafKind k);
-constexpr int kTcTile = 128;  // tensor-core leaf tile (rows and columns)
+constexpr int kTcTile = 128;      // tensor-core leaf tile (rows and columns)
+constexpr int kTcPairRows = 256;  // rows of the CTA-pair tile (columns stay kTcTile)
 
 struct PlanOptions {
     int cutoff = 64;

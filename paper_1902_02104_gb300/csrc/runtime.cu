@@ -108,6 +108,7 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
     d->split_lv = h.split_lv;
     d->comb_lv = h.comb_lv;
     d->leaf = h.leaf;
+    d->tc_pair = h.leaf != LEAF_F64 && h.tile_rows == kTcPairRows;
     return ATA_OK;
 }
 
@@ -134,10 +135,11 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h) {
     }
     for (size_t i = 0; i < P.products.size(); ++i) {
         const LeafProduct& lp = P.products[i];
-        const int tm = leaf_tile(P.leaf);
-        const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tm - 1) / tm;
+        const int tn = leaf_tile(P.leaf);
+        const int tm = P.leaf == LEAF_F64 ? tn : h->tile_rows;
+        const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tn - 1) / tn;
         for (int64_t ti = 0; ti < a; ++ti)
-            for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti : 0); tj < b; ++tj) {
+            for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti * tm / tn : 0); tj < b; ++tj) {
                 LeafTile t;
                 t.prod = p_base + (int32_t)i;
                 t.ti = (int32_t)ti;
@@ -408,7 +410,8 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     out->max_strassen_levels = P.stats.max_strassen_levels;
     out->n_leaf_products = (int32_t)P.products.size();
     int64_t tiles = 0;
-    for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, leaf_tile(P.leaf), leaf_tile(P.leaf));
+    const int tn = leaf_tile(P.leaf), tm = P.leaf == LEAF_F64 ? tn : P.tc_tile_rows;  // planned tile shape
+    for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, tm, tn);
     out->n_leaf_tiles = (int32_t)tiles;
     int64_t ns = 0, nc = 0;
     for (auto& v : P.split_levels) ns += v.size();
@@ -420,6 +423,8 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     out->classical_mults = P.m * P.n * (P.n + 1) / 2;
     out->adds = P.stats.adds;
     out->workspace_bytes = P.ws_bytes;
+    out->leaf_tile_rows = tm;
+    out->leaf_tile_cols = tn;
 }
 
 ata_status check_terms(const Plan& P) {
@@ -432,6 +437,7 @@ ata_status check_terms(const Plan& P) {
 ata_status rebuild_tables(ata_plan plan, int64_t lda) {
     HostTables h;
     h.leaf = plan->plan.leaf;
+    if (h.leaf != LEAF_F64) h.tile_rows = tc_rows_for(plan->plan);
     h.split_pending.resize(plan->plan.split_levels.size());
     h.comb_pending.resize(plan->plan.combine_levels.size());
     append_plan_tables(plan->plan, 0, lda, &h);
@@ -642,6 +648,15 @@ ata_status ata_plan_create(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype,
 ata_status ata_plan_get_info(ata_plan plan, ata_plan_info* out) {
     if (!plan || !out) return fail(ATA_EINVAL, "NULL argument");
     fill_info(plan->plan, plan->dtype, out);
+    if (plan->plan.leaf != LEAF_F64) {
+        // the tile shape that runs on this device (the CTA-pair kernel may be
+        // unavailable), and the tile count for it
+        const int tm = tc_rows_for(plan->plan);
+        int64_t tiles = 0;
+        for (const LeafProduct& lp : plan->plan.products) tiles += leaf_tiles(lp, tm, kTcTile);
+        out->n_leaf_tiles = (int32_t)tiles;
+        out->leaf_tile_rows = tm;
+    }
     return ATA_OK;
 }
 

@@ -43,6 +43,7 @@ struct PrepTask {
 // Task tables on the host, ready to upload (one plan or a merged batch).
 struct HostTables {
     LeafKind leaf = LEAF_F64;
+    int tile_rows = kTcTile;  // tensor-core leaves: kTcPairRows selects the CTA-pair kernel
     std::vector<Term> terms;
     std::vector<LeafProduct> prods;
     std::vector<LeafTile> tiles;
@@ -59,6 +60,7 @@ struct HostTables {
 // The same tables in device memory (one allocation).
 struct DeviceTables {
     LeafKind leaf = LEAF_F64;
+    bool tc_pair = false;  // tensor-core leaves run as CTA pairs (256-row tiles)
     char* blob = nullptr;
     Term* terms = nullptr;
     LeafProduct* prods = nullptr;
@@ -111,6 +113,8 @@ ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cuda
 ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d);
 bool leaf_supported(LeafKind k);
 int leaf_tile(LeafKind k);
+// Row tile of the tensor-core kernel that runs plan P on this device.
+int tc_rows_for(const Plan& P);
 
 // Planner defaults and the autotuner.
 int default_cutoff(int64_t m, int64_t n, ata_dtype dtype);

@@ -59,15 +59,14 @@ constexpr int64_t kMaxLeafProducts = 400000;
 
 double model_time(const Plan& P, ata_dtype d) {
     const Rates r = rates_for(d);
-    // tensor-core leaves compute on whole 128 x 128 tiles
+    // tensor-core leaves compute on whole tiles (128 x 128, or 256 x 128 for
+    // CTA pairs)
     double leaf = (double)P.stats.mults;
     if (P.leaf != LEAF_F64) {
         leaf = 0;
-        for (const LeafProduct& lp : P.products) {
-            const double tiles = lp.out_kind == OUT_SYRK ? (lp.p_pad / 128.0) * (lp.p_pad / 128.0 + 1) / 2
-                                                         : (lp.p_pad / 128.0) * (lp.r_pad / 128.0);
-            leaf += tiles * 128.0 * 128.0 * lp.K_pad;
-        }
+        const int tm = P.tc_tile_rows > 0 ? P.tc_tile_rows : kTcTile;
+        for (const LeafProduct& lp : P.products)
+            leaf += (double)leaf_tiles(lp, tm, kTcTile) * tm * kTcTile * lp.K_pad;
     }
     return leaf / r.leaf_fma + (double)P.stats.adds / r.add + 2.0 * (double)P.ws_bytes / r.hbm +
            prep_bytes(P) / (0.5 * r.hbm) + 2e-6 * (double)(P.split_levels.size() + P.combine_levels.size() + 1);

@@ -85,3 +85,27 @@ def test_autotune_picks_a_listed_cutoff():
     i = q(10000, 10000, 0)
     assert 64 <= i["cutoff"] <= 2048
     assert i["workspace_bytes"] <= 48 << 30
+
+
+def _upper_tiles(rows, tm, tn):
+    # brute force: tiles (ti, tj) of a rows x rows SYRK block holding an entry j >= i
+    a, b = -(-rows // tm), -(-rows // tn)
+    return sum(1 for ti in range(a) for tj in range(b)
+               if any(j >= i for i in range(ti * tm, min(rows, ti * tm + tm)) for j in (min(rows, tj * tn + tn) - 1,)))
+
+
+@pytest.mark.parametrize("n", [100, 129, 256, 300, 511, 640, 1000, 1023, 1500, 2047])
+def test_leaf_tile_shape_single_syrk_leaf(n):
+    # one diagonal leaf (n <= cutoff): 128-row tiles unless every X operand is
+    # wider than one tile and 256-row tiles cover at most 1/8 more area
+    for dtype in (ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI):
+        i = q(300, n, 4096, dtype)
+        t128 = _upper_tiles(n, 128, 128)
+        t256 = _upper_tiles(n, 256, 128)
+        pair = n > 128 and t256 * 256 <= 1.125 * t128 * 128
+        assert i["leaf_tile_cols"] == 128
+        assert i["leaf_tile_rows"] == (256 if pair else 128), (n, t128, t256)
+        assert i["n_leaf_tiles"] == (t256 if pair else t128)
+    f = q(300, n, 4096, ata.ATA_F64)
+    assert (f["leaf_tile_rows"], f["leaf_tile_cols"]) == (64, 64)
+    assert f["n_leaf_tiles"] == _upper_tiles(n, 64, 64)

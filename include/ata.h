@@ -108,6 +108,9 @@ typedef struct {
                                    ata_plan_query reports the planned shape,
                                    ata_plan_get_info the one that runs on
                                    the plan's device                        */
+    int64_t r;                  /* general product X^t Y: columns of Y (and
+                                   n = columns of X, m = rows of both);
+                                   0 for A^t A plans                        */
 } ata_plan_info;
 
 /* Status text ("ATA_OK", ...).  Never NULL. */
@@ -145,6 +148,11 @@ typedef struct {
                                     the FP64 modes, 1 for the FP32 modes)      */
     int32_t max_strassen_levels; /* cap on Strassen levels per product
                                     (-1 = none; 0 = classical products)        */
+    int32_t cta_pair;            /* tensor-core leaves: 1 = 256 x 128 output
+                                    tiles computed by CTA pairs (two SMs,
+                                    tcgen05 cta_group::2) when every leaf is
+                                    wider than 128 rows; -1 or 0 = 128 x 128
+                                    tiles on single CTAs (default)           */
 } ata_plan_options;
 
 /* Same as ata_plan_create with explicit options (opts may not be NULL).
@@ -219,6 +227,49 @@ ata_status ata_plan_device_status(ata_plan plan, int* code);
 
 /* Release the plan (waits for its queued work first). */
 void ata_plan_destroy(ata_plan plan);
+
+/* ---------------------------------------------------------------------------
+ * General product C = X^t Y: the HASA step of Section 4.2.2 as an entry point
+ * of its own (the off-diagonal block C_12 = A_L^t A_R of the recursion is one
+ * such product).  X is m x p and Y is m x r, row-major with leading
+ * dimensions ldx >= p and ldy >= r (FP64 for ATA_F64 / ATA_F64_OZAKI, FP32
+ * for ATA_F32_BF16X3 / ATA_F32_TF32, as A above); C is p x r, row-major FP64
+ * with ldc >= r, every entry written.  Strassen levels (Section 4.2.2, with
+ * the corrected M1 and M7, or Winograd's variant) run while min(p, m, r) >
+ * cutoff, halving all three with ceil/floor and implicit zero padding; the
+ * leaves are the same kernels as A^t A's off-diagonal products.  Plans are
+ * ata_plan objects: ata_plan_get_info, ata_plan_workspace_size, stage
+ * timing, ata_plan_device_status and ata_plan_destroy apply; ata_execute,
+ * ata_execute_host and ata_execute_batched reject them (ATA_EINVAL).
+ * opts may be NULL (all defaults, cutoff autotuned).
+ * -------------------------------------------------------------------------*/
+
+/* Planner only (no device call); info.n = p, info.r = r,
+ * info.classical_mults = m p r.  Errors: ATA_EINVAL (negative sizes, a size
+ * >= 2^31, bad dtype or options, NULL out). */
+ata_status ata_gemm_query(int64_t m, int64_t p, int64_t r, ata_dtype dtype,
+                          const ata_plan_options* opts, ata_plan_info* out);
+
+/* Host check of the plan's tables: every term inside X, Y or the workspace,
+ * every workspace range inside the workspace, every entry of C written
+ * exactly once (checked up to 2^24 entries).  Errors: ATA_EINVAL with the
+ * first violation in ata_last_error_message(). */
+ata_status ata_gemm_plan_check(int64_t m, int64_t p, int64_t r, ata_dtype dtype,
+                               const ata_plan_options* opts);
+
+/* Build a general-product plan on the current device (workspace allocated
+ * here).  Errors: as ata_gemm_query, plus ATA_ENOMEM, ATA_ECUDA. */
+ata_status ata_gemm_plan_create(ata_plan* out, int64_t m, int64_t p, int64_t r,
+                                ata_dtype dtype, const ata_plan_options* opts);
+
+/* C = X^t Y, queued on `stream` (device pointers; layouts above; X and Y
+ * not modified).  The first call, and a call with other leading dimensions,
+ * captures the plan's graph.  Errors: ATA_EINVAL (an A^t A plan, ldx < p,
+ * ldy < r, ldc < r, NULL X or Y with m p r > 0, NULL C with p r > 0,
+ * pointers not aligned to their element size), ATA_ECUDA. */
+ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx,
+                       const void* Y, int64_t ldy, double* C, int64_t ldc,
+                       void* stream);
 
 /* C_packed = A^t A (FP64, as ata_execute with ATA_F64 and the given
  * cutoff) without allocating any device memory.  The paper has no

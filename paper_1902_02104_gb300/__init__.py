@@ -44,7 +44,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_sum_tasks", ctypes.c_int32), ("n_combine_tasks", ctypes.c_int32),
                 ("n_launches", ctypes.c_int32), ("mults", ctypes.c_int64), ("classical_mults", ctypes.c_int64),
                 ("adds", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("leaf_tile_rows", ctypes.c_int32), ("leaf_tile_cols", ctypes.c_int32)]
+                ("leaf_tile_rows", ctypes.c_int32), ("leaf_tile_cols", ctypes.c_int32), ("r", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -52,7 +52,7 @@ class PlanInfo(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int32), ("variant", ctypes.c_int32), ("fuse_levels", ctypes.c_int32),
-                ("max_strassen_levels", ctypes.c_int32)]
+                ("max_strassen_levels", ctypes.c_int32), ("cta_pair", ctypes.c_int32)]
 
 
 _lib = None
@@ -80,6 +80,10 @@ def load():
         "ata_plan_create": ([ctypes.POINTER(vp), i64, i64, i32, i32], i32),
         "ata_plan_create_opts": ([ctypes.POINTER(vp), i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
         "ata_plan_check": ([i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
+        "ata_gemm_query": ([i64, i64, i64, i32, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanInfo)], i32),
+        "ata_gemm_plan_check": ([i64, i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
+        "ata_gemm_plan_create": ([ctypes.POINTER(vp), i64, i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
+        "ata_gemm_tn": ([vp, vp, i64, vp, i64, dp, i64, vp], i32),
         "ata_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i32),
         "ata_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "ata_execute": ([vp, vp, i64, dp, vp], i32),
@@ -122,8 +126,8 @@ def _dtype_code(dtype) -> int:
     return int(dtype)
 
 
-def _opts(cutoff=0, variant=-1, fuse_levels=-1, max_strassen_levels=-1) -> PlanOptions:
-    return PlanOptions(int(cutoff), int(variant), int(fuse_levels), int(max_strassen_levels))
+def _opts(cutoff=0, variant=-1, fuse_levels=-1, max_strassen_levels=-1, cta_pair=-1) -> PlanOptions:
+    return PlanOptions(int(cutoff), int(variant), int(fuse_levels), int(max_strassen_levels), int(cta_pair))
 
 
 def ata_plan_query(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> dict:
@@ -203,6 +207,66 @@ class Plan:
 
 def ata_plan_create(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> Plan:
     return Plan(m, n, dtype, cutoff, **opts)
+
+
+class GemmPlan(Plan):
+    """A general-product plan: ``GemmPlan(m, p, r, dtype, cutoff)`` then
+    ``plan(X, Y, C)`` for C = X^t Y (X: m x p, Y: m x r, C: p x r FP64)."""
+
+    def __init__(self, m: int, p: int, r: int, dtype=ATA_F64, cutoff: int = 0, **opts):
+        self.m, self.n, self.r, self.dtype = int(m), int(p), int(r), _dtype_code(dtype)
+        h = ctypes.c_void_p()
+        o = _opts(cutoff, **opts)
+        _check(load().ata_gemm_plan_create(ctypes.byref(h), self.m, self.n, self.r, self.dtype, ctypes.byref(o)))
+        self.handle = h
+
+    def __call__(self, X, Y, C=None, stream=None):
+        return ata_gemm_tn(self, X, Y, C, stream)
+
+
+def ata_gemm_plan_create(m: int, p: int, r: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> GemmPlan:
+    return GemmPlan(m, p, r, dtype, cutoff, **opts)
+
+
+def ata_gemm_query(m: int, p: int, r: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> dict:
+    info = PlanInfo()
+    o = _opts(cutoff, **opts)
+    _check(load().ata_gemm_query(m, p, r, _dtype_code(dtype), ctypes.byref(o), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def ata_gemm_plan_check(m: int, p: int, r: int, dtype=ATA_F64, cutoff: int = 0, **opts):
+    """Host-side bounds and coverage check of a general-product plan (raises AtaError)."""
+    o = _opts(cutoff, **opts)
+    _check(load().ata_gemm_plan_check(m, p, r, _dtype_code(dtype), ctypes.byref(o)))
+
+
+def _operand_ld(T, rows, cols, name, in_dtype):
+    if not T.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if T.dtype != in_dtype:
+        raise TypeError(f"{name} must be {in_dtype} for this plan")
+    if T.dim() != 2 or tuple(T.shape) != (rows, cols):
+        raise ValueError(f"{name} must be {rows} x {cols}")
+    if rows > 0 and cols > 0 and T.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    return max(T.stride(0), cols, 1) if rows > 1 else max(cols, 1)
+
+
+def ata_gemm_tn(plan: GemmPlan, X, Y, C=None, stream=None):
+    """C = X^t Y on the GPU (X: m x p, Y: m x r row-major CUDA tensors; C a
+    p x r float64 CUDA tensor, allocated when None).  Asynchronous on `stream`."""
+    import torch
+    ldx = _operand_ld(X, plan.m, plan.n, "X", plan.in_dtype)
+    ldy = _operand_ld(Y, plan.m, plan.r, "Y", plan.in_dtype)
+    if C is None:
+        C = torch.empty((plan.n, plan.r), dtype=torch.float64, device=X.device)
+    if C.dtype != torch.float64 or tuple(C.shape) != (plan.n, plan.r) or (plan.n > 0 and plan.r > 0 and C.stride(1) != 1):
+        raise ValueError("C must be a row-major float64 tensor of p x r")
+    ldc = max(C.stride(0), plan.r, 1) if plan.n > 1 else max(plan.r, 1)
+    _check(load().ata_gemm_tn(plan.handle, ctypes.c_void_p(X.data_ptr()), ldx, ctypes.c_void_p(Y.data_ptr()), ldy,
+                              ctypes.c_void_p(C.data_ptr()), ldc, _stream_handle(stream)))
+    return C
 
 
 def ata_plan_destroy(plan: Plan):

@@ -56,6 +56,7 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
     for (int i = 0; i < count; ++i) {
         if (!plans[i]) return fail(ATA_EINVAL, "NULL plan in batch");
         const Plan& P = plan_of(plans[i]);
+        if (P.gemm) return fail(ATA_EINVAL, "general-product plans run through ata_gemm_tn");
         if (P.leaf != leaf) return fail(ATA_EINVAL, "plans of one batch must share the dtype family");
         if (lda[i] < P.n || lda[i] < 1) return fail(ATA_EINVAL, "lda[i] must be >= max(n_i, 1)");
         if (P.m > 0 && P.n > 0 && !A[i]) return fail(ATA_EINVAL, "A[i] is NULL");

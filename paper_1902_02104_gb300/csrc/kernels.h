@@ -6,10 +6,11 @@
 
 namespace ata {
 
-// Device pointers an execution binds: the caller's A and C and the plan's
-// workspace, per instance.  Kernels receive a BindSet by value (a
-// __grid_constant__ parameter), so a launch snapshots its pointers and a
-// captured graph is re-pointed by updating kernel-node parameters.
+// Device pointers an execution binds: the caller's A (X of a general
+// product), Y (general product only) and C, and the plan's workspace, per
+// instance.  Kernels receive a BindSet by value (a __grid_constant__
+// parameter), so a launch snapshots its pointers and a captured graph is
+// re-pointed by updating kernel-node parameters.
 struct Bind {
     const void* A;
     double* C;
@@ -19,7 +20,15 @@ struct Bind {
     // elements of A, bytes of W, elements of C
     int64_t a_elems, w_bytes, c_elems;
     int64_t check;
+    const void* B;
+    int64_t b_elems;
 };
+
+// Base of the buffer a term reads (A, Y of a general product, or W).
+template <typename T>
+__host__ __device__ __forceinline__ const T* term_base(const Bind& b, int8_t buf) {
+    return reinterpret_cast<const T*>(buf == BUF_A ? b.A : buf == BUF_B ? b.B : static_cast<const void*>(b.W));
+}
 
 constexpr int kMaxBatchBind = 256;  // instances per batched launch (16 KB of parameters)
 

@@ -21,8 +21,7 @@ __device__ __forceinline__ int64_t packed_start(int64_t i, int64_t n) { return i
 template <typename T>
 __device__ __forceinline__ const T* term_ptr(const Bind& b, const Term& t) {
     // b is the instance of the term (t.inst)
-    const T* base = t.buf == BUF_A ? reinterpret_cast<const T*>(b.A) : reinterpret_cast<const T*>(b.W);
-    return base + t.off;
+    return term_base<T>(b, t.buf) + t.off;
 }
 
 // Value of a fused operand (sum of signed terms) at (k, c); zero outside
@@ -34,7 +33,10 @@ __device__ __forceinline__ const T* term_ptr(const Bind& b, const Term& t) {
 // and `code` is recorded in *status.
 __device__ __forceinline__ bool in_bounds(const Bind& b, int8_t buf, int64_t idx, int es, int* status, int code) {
     if (!b.check) return true;
-    const int64_t lim = buf == BUF_A ? b.a_elems : buf == BUF_W ? b.w_bytes / es : b.c_elems;
+    const int64_t lim = buf == BUF_A   ? b.a_elems
+                        : buf == BUF_B ? b.b_elems
+                        : buf == BUF_W ? b.w_bytes / es
+                                       : b.c_elems;
     if (idx >= 0 && idx < lim) return true;
     atomicCAS(status, 0, code);
     return false;
@@ -191,6 +193,9 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
                     if (sp.out_kind == OUT_DENSE) {
                         const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
                         if (in_bounds(bind, BUF_W, idx, 8, status, 12)) reinterpret_cast<double*>(bind.W)[idx] = acc[a][b];
+                    } else if (sp.out_kind == OUT_CDENSE) {
+                        const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
+                        if (in_bounds(bind, BUF_C, idx, 8, status, 12)) bind.C[idx] = acc[a][b];
                     } else {
                         const int64_t gi = (int64_t)sp.ci0 + i, gj = (int64_t)sp.cj0 + j;
                         if (sp.out_kind == OUT_SYRK && gj < gi) continue;
@@ -320,6 +325,9 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Bi
             if (ct.dst_kind == OUT_DENSE) {
                 const int64_t idx = ct.dst_off + (int64_t)ii * ct.dst_ld + jj;
                 if (in_bounds(bind, BUF_W, idx, 8, status, 32)) reinterpret_cast<double*>(bind.W)[idx] = d[q];
+            } else if (ct.dst_kind == OUT_CDENSE) {
+                const int64_t idx = ct.dst_off + (int64_t)ii * ct.dst_ld + jj;
+                if (in_bounds(bind, BUF_C, idx, 8, status, 32)) bind.C[idx] = d[q];
             } else {
                 const int64_t gi = (int64_t)ct.ci0 + ii, gj = (int64_t)ct.cj0 + jj;
                 const int64_t idx = packed_start(gi, bind.n) + (gj - gi);

@@ -11,9 +11,8 @@
 // Part products are exact in FP32.  The tensor core accumulates in FP32
 // with truncation, so an accumulator that runs over a long K drifts by a
 // relative ~2^-23 per addition.  Orders whose share of the result is large
-// are therefore accumulated per K chunk of 256 in their own accumulator, in
-// which every partial sum is an integer of at most 2^24 units (a leading-digit
-// product is at most 2^16 units, so 256 of them stay exact), and drained
+// are therefore accumulated per K chunk in their own accumulator, in which
+// every partial sum is an integer of at most 2^24 units, and drained
 // into float-float (hi, lo) sums by the epilogue after each chunk: orders 0-1
 // for bf16x3, 0-2 for ozaki.  The remaining orders (2 for bf16x3: ~2^-16 of
 // the result, accumulated over the whole K; 3-5 for ozaki, drained per chunk)
@@ -297,12 +296,15 @@ __device__ __forceinline__ long long f2d_bits(float f) {
 }
 
 // Scale exponent E of a column whose largest magnitude has bit pattern mx:
-// mx = f * 2^E with f in [0.5, 1); 0 for an all-zero (or subnormal) column;
-// kNonFinite when the column holds an Inf or NaN (its products become NaN).
+// mx = f * 2^(E - HEAD) with f in [0.5, 1), so that every |x| 2^-E of the
+// column is below 2^-HEAD (HEAD bits of headroom shrink the leading digit);
+// 0 for an all-zero (or subnormal) column; kNonFinite when the column holds
+// an Inf or NaN (its products become NaN).
 constexpr int kNonFinite = 1 << 20;
+template <int HEAD>
 __device__ __forceinline__ int col_exponent(unsigned long long mx) {
     const int eb = (int)((mx >> 52) & 0x7FF);
-    return eb == 0 ? 0 : eb == 0x7FF ? kNonFinite : eb - 1022;
+    return eb == 0 ? 0 : eb == 0x7FF ? kNonFinite : eb - 1022 + HEAD;
 }
 
 // K-major shared-memory matrix descriptor (tcgen05 "matrix descriptor"):
@@ -351,13 +353,20 @@ struct Geo;
 
 // D group: orders 0..DMAX, order d into accumulator min(d, ND - 1), drained
 // after every chunk of KC; accumulator 0 holds order 0 alone and is exact.
+// Exactness bounds the chunk: with |d0| <= 256 a leading-digit product is at
+// most 2^16 units, so KC = 256 keeps order 0 within 2^24; orders 1 and 2 add
+// at most 2^16 and 5 * 2^13 units per K index.  HEAD bits of headroom would
+// allow longer chunks (HEAD = 2: KC = 512 for orders 0-2) but shift the
+// representation down by HEAD bits, so the inexact F group carries 2^HEAD
+// times more of the result; for the FP64 emulation that F error over 512-deep
+// chunks exceeds the 1e-11 bound, so HEAD stays 0.
 // DBUF > 1 double-buffers the D group.  F group: orders FMIN..FMAX in one
 // accumulator, over the whole K (F_FINAL) or drained per chunk.
 template <>
 struct Geo<MODE_BF16X3> {
     static constexpr int PARTS = 3, ELEM = 2, KBLK = 32, ROWB = 64, KSTEP = 16, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 4, SBO = 512;  // 64B swizzle
-    static constexpr int KC = 256, ND = 2, DMAX = 2, DBUF = 2, FMIN = 1, FMAX = 0;  // no F group
+    static constexpr int KC = 256, ND = 2, DMAX = 2, DBUF = 2, FMIN = 1, FMAX = 0, HEAD = 0;  // no F group
     static constexpr bool F_FINAL = false, SLICED = true;
     static constexpr int EPI_WARPS = 16;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 0;
@@ -368,7 +377,7 @@ template <>
 struct Geo<MODE_TF32> {
     static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6, NSTAGE2 = 8;
     static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
-    static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0;
+    static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0, HEAD = 0;
     static constexpr bool F_FINAL = true, SLICED = false;
     static constexpr int EPI_WARPS = 8;
     static constexpr uint32_t TMEM_COLS = 128, F_COL = 0;
@@ -379,7 +388,7 @@ template <>
 struct Geo<MODE_OZAKI> {
     static constexpr int PARTS = 6, ELEM = 2, KBLK = 16, ROWB = 32, KSTEP = 16, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 6, SBO = 256;  // 32B swizzle
-    static constexpr int KC = 256, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5;
+    static constexpr int KC = 256, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5, HEAD = 0;
     static constexpr bool F_FINAL = false, SLICED = true;
     static constexpr int EPI_WARPS = 16;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 384;
@@ -453,7 +462,7 @@ __device__ __forceinline__ void load_operand_regs(const BindSet<NB>& bs, const T
     for (int t = 0; t < nt; ++t) {
         const Term tm = terms[t0 + t];
         const Bind& b = bs.b[tm.inst];
-        const TS* base = tm.buf == BUF_A ? reinterpret_cast<const TS*>(b.A) : reinterpret_cast<const TS*>(b.W);
+        const TS* base = term_base<TS>(b, tm.buf);
         const int c = c0 + vc;
         const TS* colp = base + tm.off + c;
         const int kmax = min(K, tm.rows);
@@ -563,7 +572,8 @@ __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ 
 }
 
 // Balanced base-256 digits of round(x * 2^(8S - E)), most significant first:
-// x * 2^-E ~= sum_s d[s] * 2^(-8(s+1)), |d[0]| <= 256, |d[s>0]| <= 128.
+// x * 2^-E ~= sum_s d[s] * 2^(-8(s+1)), |d[0]| <= 256 >> HEAD (E carries the
+// column's headroom), |d[s>0]| <= 128.
 // Integer arithmetic only (the FP64 pipe is not involved).
 template <int S>
 __device__ __forceinline__ void slice_digits(double x, int E, int (&d)[S]) {
@@ -662,7 +672,7 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
             constexpr int S = Geo<MODE>::PARTS;
             const unsigned long long mx =
                 reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
-            const int E = col_exponent(mx);
+            const int E = col_exponent<Geo<MODE>::HEAD>(mx);
             int dg[8][S];
 #pragma unroll
             for (int i = 0; i < 8; ++i) slice_digits(tile[kc * 8 + i][col], E, dg[i]);
@@ -988,9 +998,10 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
             const bool row_ok = i < pr->out_rows;
             int Ei = 0;
             if constexpr (G::SLICED) {
-                if (row_ok) Ei = col_exponent(reinterpret_cast<const unsigned long long*>(pr->ex)[i]);
+                if (row_ok) Ei = col_exponent<G::HEAD>(reinterpret_cast<const unsigned long long*>(pr->ex)[i]);
             }
-            double* dense = reinterpret_cast<double*>(bind.W) + pr->out_off + (int64_t)i * pr->out_ld;
+            double* dense = (pr->out_kind == OUT_CDENSE ? bind.C : reinterpret_cast<double*>(bind.W)) + pr->out_off +
+                            (int64_t)i * pr->out_ld;
             const int64_t gi = (int64_t)pr->ci0 + i;
             double* prow = bind.C + (packed_start(gi, bind.n) - gi + pr->cj0);
 #pragma unroll
@@ -1013,7 +1024,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                             long long bh = f2d_bits(hh), bl = f2d_bits(ll);
                             double v;
                             if constexpr (G::SLICED) {
-                                const int sc = Ei + col_exponent(reinterpret_cast<const unsigned long long*>(pr->ey)[j]);
+                                const int sc = Ei + col_exponent<G::HEAD>(reinterpret_cast<const unsigned long long*>(pr->ey)[j]);
                                 if (bh) bh += (long long)sc << 52;
                                 if (bl) bl += (long long)sc << 52;
                                 v = sc >= kNonFinite ? __longlong_as_double(0x7FF8000000000000LL)
@@ -1021,7 +1032,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                             } else {
                                 v = __longlong_as_double(bh) + __longlong_as_double(bl);
                             }
-                            if (pr->out_kind == OUT_DENSE) {
+                            if (pr->out_kind == OUT_DENSE || pr->out_kind == OUT_CDENSE) {
                                 dense[j] = v;
                             } else if (pr->out_kind == OUT_PACKED || (int64_t)pr->cj0 + j >= gi) {
                                 prow[j] = v;
@@ -1214,7 +1225,7 @@ ata_status tc_prepare_device() {
             if (err == cudaSuccess) err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
             if (g_sms <= 0) g_sms = 1;
         }
-        if (err == cudaSuccess && !std::getenv("ATA_NO_CTA_PAIR")) {
+        if (err == cudaSuccess) {
             g_pair_clusters[MODE_BF16X3] = pair_clusters<MODE_BF16X3>();
             g_pair_clusters[MODE_TF32] = pair_clusters<MODE_TF32>();
             g_pair_clusters[MODE_OZAKI] = pair_clusters<MODE_OZAKI>();

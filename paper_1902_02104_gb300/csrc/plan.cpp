@@ -144,7 +144,7 @@ void emit_leaf(Ctx& c, const std::vector<Term>& X, const std::vector<Term>& Y, i
         const TcGeom g = tc_geom(P.leaf);
         // X rows of a leaf above one tile are padded to whole CTA-pair tiles
         // (256 rows); a SYRK leaf reads the same buffer as Y
-        const int64_t xr = p > kTcTile ? kTcPairRows : kTcTile;
+        const int64_t xr = c.opt->cta_pair && p > kTcTile ? kTcPairRows : kTcTile;
         lp.p_pad = (int32_t)((p + xr - 1) / xr * xr);
         lp.r_pad = syrk ? lp.p_pad : (int32_t)((r + kTcTile - 1) / kTcTile * kTcTile);
         lp.K_pad = (int32_t)std::max<int64_t>((K + g.k_align - 1) / g.k_align * g.k_align, g.k_align);
@@ -345,15 +345,9 @@ int64_t leaf_tiles(const LeafProduct& p, int tm, int tn) {
     return a * b;
 }
 
-bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::string* err) {
-    if (m < 0 || n < 0) {
-        *err = "m and n must be >= 0";
-        return false;
-    }
-    if (m > INT32_MAX || n > INT32_MAX) {
-        *err = "m and n must be < 2^31";
-        return false;
-    }
+namespace {
+
+bool check_options(const PlanOptions& opt, std::string* err) {
     if (opt.cutoff < 16 || opt.cutoff > 4096) {
         *err = "cutoff must be in [16, 4096]";
         return false;
@@ -362,7 +356,10 @@ bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::st
         *err = "variant must be 0 (Strassen) or 1 (Winograd)";
         return false;
     }
-    Plan& P = *out;
+    return true;
+}
+
+void start_plan(Plan& P, int64_t m, int64_t n, const PlanOptions& opt) {
     P = Plan();
     P.m = m;
     P.n = n;
@@ -373,10 +370,9 @@ bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::st
     P.sum_dt = P.in_dt;
     P.fuse_levels = std::max(0, opt.fuse_levels);
     P.max_levels = std::max(0, opt.max_levels);
-    Ctx c;
-    c.P = &P;
-    c.opt = &opt;
-    if (n > 0) recurse_columns(c, 0, n, 0);
+}
+
+void finish_plan(Plan& P, const Ctx& c, const PlanOptions& opt) {
     P.ws_bytes = c.ws;
     if (P.leaf != LEAF_F64) {
         // CTA-pair tiles when every X operand is padded to them and they add
@@ -388,8 +384,79 @@ bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::st
             a1 += (double)leaf_tiles(lp, kTcTile, kTcTile) * kTcTile * kTcTile;
             a2 += (double)leaf_tiles(lp, kTcPairRows, kTcTile) * kTcPairRows * kTcTile;
         }
-        P.tc_tile_rows = all && a2 <= 1.125 * a1 ? kTcPairRows : kTcTile;
+        P.tc_tile_rows = opt.cta_pair && all && a2 <= 1.125 * a1 ? kTcPairRows : kTcTile;
     }
+}
+
+}  // namespace
+
+bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::string* err) {
+    if (m < 0 || n < 0) {
+        *err = "m and n must be >= 0";
+        return false;
+    }
+    if (m > INT32_MAX || n > INT32_MAX) {
+        *err = "m and n must be < 2^31";
+        return false;
+    }
+    if (!check_options(opt, err)) return false;
+    Plan& P = *out;
+    start_plan(P, m, n, opt);
+    Ctx c;
+    c.P = &P;
+    c.opt = &opt;
+    if (n > 0) recurse_columns(c, 0, n, 0);
+    finish_plan(P, c, opt);
+    return true;
+}
+
+bool build_gemm_plan(int64_t m, int64_t p, int64_t r, const PlanOptions& opt, Plan* out, std::string* err) {
+    if (m < 0 || p < 0 || r < 0) {
+        *err = "m, p and r must be >= 0";
+        return false;
+    }
+    if (m > INT32_MAX || p > INT32_MAX || r > INT32_MAX) {
+        *err = "m, p and r must be < 2^31";
+        return false;
+    }
+    if (!check_options(opt, err)) return false;
+    Plan& P = *out;
+    start_plan(P, m, p, opt);
+    P.gemm = true;
+    P.r = r;
+    Ctx c;
+    c.P = &P;
+    c.opt = &opt;
+    if (p > 0 && r > 0) {
+        // X and Y as whole operands (planned with dense leading dimensions p
+        // and r; the runtime rebases them to the caller's ldx, ldy), the
+        // output a dense p x r block of C (planned ld r, rebased to ldc)
+        Term x{}, y{};
+        x.off = 0;
+        x.ld = p;
+        x.rows = (int32_t)m;
+        x.cols = (int32_t)p;
+        x.buf = BUF_A;
+        x.dt = P.in_dt;
+        y = x;
+        y.ld = r;
+        y.cols = (int32_t)r;
+        y.buf = BUF_B;
+        std::vector<Term> X, Y;
+        if (m > 0) {
+            X.push_back(x);
+            Y.push_back(y);
+        }
+        Target t{};
+        t.kind = OUT_CDENSE;
+        t.off = 0;
+        t.ld = (int32_t)r;
+        const int s = strassen_levels(p, m, r, P.cutoff, P.max_levels);
+        P.stats.max_strassen_levels = s;
+        P.stats.n_nodes = 1;
+        expand(c, X, Y, p, m, r, m, 0, s, t, P.in_dt, P.in_dt);
+    }
+    finish_plan(P, c, opt);
     return true;
 }
 

@@ -34,7 +34,9 @@
 
 namespace ata {
 
-enum BufId : int8_t { BUF_A = 0, BUF_W = 1, BUF_C = 2 };
+// Buffers a term or an output refers to: the caller's A (or X of a general
+// product), the plan workspace W, the caller's C, and Y of a general product.
+enum BufId : int8_t { BUF_A = 0, BUF_W = 1, BUF_C = 2, BUF_B = 3 };
 enum ElemType : int8_t { DT_F64 = 0, DT_F32 = 1 };
 
 // Leaf arithmetic family of a plan.
@@ -52,7 +54,10 @@ struct Term {
 };
 static_assert(sizeof(Term) == 32, "Term layout");
 
-enum OutKind : int8_t { OUT_DENSE = 0, OUT_PACKED = 1, OUT_SYRK = 2 };
+// Output of a leaf or combine: a dense block of W, a block of packed C, the
+// upper part of a diagonal block of packed C, or a dense block of the
+// caller's C (general product; leading dimension ldc after rebasing).
+enum OutKind : int8_t { OUT_DENSE = 0, OUT_PACKED = 1, OUT_SYRK = 2, OUT_CDENSE = 3 };
 
 // Leaf product: out(p x r) = X^t Y, X and Y sums of terms (K rows each).
 struct LeafProduct {
@@ -107,6 +112,10 @@ struct PlanStats {
 
 struct Plan {
     int64_t m = 0, n = 0;
+    // general product C = X^t Y (X: m x n, Y: m x r), the HASA entry point;
+    // false: C = A^t A (A: m x n)
+    bool gemm = false;
+    int64_t r = 0;
     int cutoff = 0;
     int variant = 0;
     LeafKind leaf = LEAF_F64;
@@ -141,10 +150,16 @@ struct PlanOptions {
     LeafKind leaf = LEAF_F64;
     int fuse_levels = 1;
     int max_levels = 64;
+    bool cta_pair = false;  // tensor-core leaves on 256 x 128 CTA-pair tiles where eligible
 };
 
 // Builds the plan.  Returns false and sets *err on invalid input.
 bool build_plan(int64_t m, int64_t n, const PlanOptions& opt, Plan* out, std::string* err);
+
+// Builds the plan of the general product C = X^t Y, X: m x p, Y: m x r, C:
+// p x r dense (Section 4.2.2's HASA on two operands): Strassen levels while
+// min(p, m, r) > cutoff (halving all three), leaf products below.
+bool build_gemm_plan(int64_t m, int64_t p, int64_t r, const PlanOptions& opt, Plan* out, std::string* err);
 
 // Number of output tiles of `p` for a leaf tile of tm x tn (upper tiles only for SYRK).
 int64_t leaf_tiles(const LeafProduct& p, int tm, int tn);

@@ -114,15 +114,22 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
 
 // Appends plan `P` (instance `inst`, A leading dimension `lda`) to host tables.
 // Tables of several plans concatenate level by level (batched execution).
-void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h) {
+void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h, int64_t ldb, int64_t ldc) {
     const int32_t t_base = (int32_t)h->terms.size();
     const int32_t p_base = (int32_t)h->prods.size();
+    // offsets planned for dense A (ld n), Y (ld r) and C (ld r) move to the
+    // caller's leading dimensions
+    auto rebase = [](int64_t off, int64_t planned_ld, int64_t ld) {
+        return planned_ld > 0 ? off / planned_ld * ld + off % planned_ld : off;
+    };
     auto fix_term = [&](Term t) {
         t.inst = inst;
         if (t.buf == BUF_A && P.n > 0) {
-            const int64_t row = t.off / P.n, col = t.off % P.n;
-            t.off = row * lda + col;
+            t.off = rebase(t.off, P.n, lda);
             t.ld = lda;
+        } else if (t.buf == BUF_B && P.r > 0) {
+            t.off = rebase(t.off, P.r, ldb);
+            t.ld = ldb;
         }
         return t;
     };
@@ -131,6 +138,10 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h) {
         lp.x0 += t_base;
         lp.y0 += t_base;
         lp.inst = inst;
+        if (lp.out_kind == OUT_CDENSE) {
+            lp.out_off = rebase(lp.out_off, P.r, ldc);
+            lp.out_ld = (int32_t)ldc;
+        }
         h->prods.push_back(lp);
     }
     for (size_t i = 0; i < P.products.size(); ++i) {
@@ -159,6 +170,10 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h) {
     for (size_t l = 0; l < P.combine_levels.size(); ++l)
         for (CombineTask ct : P.combine_levels[l]) {
             ct.inst = inst;
+            if (ct.dst_kind == OUT_CDENSE) {
+                ct.dst_off = rebase(ct.dst_off, P.r, ldc);
+                ct.dst_ld = (int32_t)ldc;
+            }
             h->comb_pending[l].push_back(ct);
         }
 }
@@ -309,7 +324,8 @@ void GraphCache::release() {
 bool same_binds(const std::vector<Bind>& a, const Bind* b, int nb) {
     if ((int)a.size() != nb) return false;
     for (int i = 0; i < nb; ++i)
-        if (a[i].A != b[i].A || a[i].C != b[i].C || a[i].W != b[i].W || a[i].n != b[i].n) return false;
+        if (a[i].A != b[i].A || a[i].B != b[i].B || a[i].C != b[i].C || a[i].W != b[i].W || a[i].n != b[i].n)
+            return false;
     return true;
 }
 
@@ -339,7 +355,8 @@ struct ata_plan_s {
     ata_dtype dtype = ATA_F64;
     int device = 0;
     char* ws = nullptr;
-    int64_t lda = -1;           // leading dimension the device tables are built for
+    int64_t lda = -1;           // leading dimensions the device tables are built for
+    int64_t ldb = -1, ldc = -1; // (Y and C: general products only)
     DeviceTables tables;
     GraphCache graph;
     std::mutex mu;
@@ -381,11 +398,13 @@ ata_status make_options(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_op
     if (u.fuse_levels < -1 || u.fuse_levels > 16) return fail(ATA_EINVAL, "fuse_levels must be -1 or in [0, 16]");
     if (u.max_strassen_levels < -1 || u.max_strassen_levels > 64)
         return fail(ATA_EINVAL, "max_strassen_levels must be -1 or in [0, 64]");
+    if (u.cta_pair < -1 || u.cta_pair > 1) return fail(ATA_EINVAL, "cta_pair must be -1, 0 or 1");
     o->leaf = leaf_of(dtype);
     o->variant = variant;
     o->cutoff = cutoff != 0 ? cutoff : default_cutoff(m, n, dtype);
     o->fuse_levels = u.fuse_levels >= 0 ? u.fuse_levels : default_fuse_levels(dtype, variant);
     o->max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : 64;
+    o->cta_pair = u.cta_pair == 1;
     return ATA_OK;
 }
 
@@ -395,6 +414,7 @@ ata_plan_options default_opts(int cutoff, int variant) {
     u.variant = variant;
     u.fuse_levels = -1;
     u.max_strassen_levels = -1;
+    u.cta_pair = -1;
     return u;
 }
 
@@ -420,11 +440,15 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     out->n_combine_tasks = (int32_t)nc;
     out->n_launches = (int32_t)(P.split_levels.size() + P.combine_levels.size() + (P.products.empty() ? 0 : 1));
     out->mults = P.stats.mults;
-    out->classical_mults = P.m * P.n * (P.n + 1) / 2;
+    out->classical_mults = P.m * P.n * (P.n + 1) / 2;  // A^t A: the upper triangle
     out->adds = P.stats.adds;
     out->workspace_bytes = P.ws_bytes;
     out->leaf_tile_rows = tm;
     out->leaf_tile_cols = tn;
+    if (P.gemm) {
+        out->r = P.r;
+        out->classical_mults = P.m * P.n * P.r;
+    }
 }
 
 ata_status check_terms(const Plan& P) {
@@ -434,13 +458,13 @@ ata_status check_terms(const Plan& P) {
     return ATA_OK;
 }
 
-ata_status rebuild_tables(ata_plan plan, int64_t lda) {
+ata_status rebuild_tables(ata_plan plan, int64_t lda, int64_t ldb = 0, int64_t ldc = 0) {
     HostTables h;
     h.leaf = plan->plan.leaf;
     if (h.leaf != LEAF_F64) h.tile_rows = tc_rows_for(plan->plan);
     h.split_pending.resize(plan->plan.split_levels.size());
     h.comb_pending.resize(plan->plan.combine_levels.size());
-    append_plan_tables(plan->plan, 0, lda, &h);
+    append_plan_tables(plan->plan, 0, lda, &h, ldb, ldc);
     finalize_tables(&h, plan->plan.in_dt, plan->plan.sum_dt);
     ata_status st = upload_tables(h, &plan->tables);
     if (st != ATA_OK) return st;
@@ -449,6 +473,8 @@ ata_status rebuild_tables(ata_plan plan, int64_t lda) {
         if (st != ATA_OK) return st;
     }
     plan->lda = lda;
+    plan->ldb = ldb;
+    plan->ldc = ldc;
     plan->graph.release();
     return ATA_OK;
 }
@@ -501,27 +527,26 @@ ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype, const ata_
     return ATA_OK;
 }
 
-ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
-    if (!opts) return fail(ATA_EINVAL, "NULL argument");
-    PlanOptions o;
-    ata_status st = make_options(m, n, dtype, *opts, &o);
-    if (st != ATA_OK) return st;
-    if (opts->cutoff == 0) {
-        st = autotune_cutoff(m, n, dtype, o.variant, &o);
-        if (st != ATA_OK) return st;
-    }
-    Plan P;
-    std::string err;
-    if (!build_plan(m, n, o, &P, &err)) return fail(ATA_EINVAL, err);
+}  // extern "C"
+
+namespace {
+
+// Host check of a built plan's tables: every term inside its buffer, every
+// workspace range inside the workspace, and every output entry written
+// exactly once (packed upper C of A^t A, or dense p x r C of a general
+// product; the coverage check runs up to 2^24 entries).
+ata_status check_plan_tables(const Plan& P) {
     const int64_t ws = P.ws_bytes;
+    const int64_t n = P.n;
     char msg[256];
     auto term_ok = [&](const Term& t, const char* what) -> bool {
         if (t.rows <= 0 || t.cols <= 0) return true;
-        if (t.buf == BUF_A) {
-            const int64_t r0 = P.n ? t.off / P.n : 0, c0 = P.n ? t.off % P.n : 0;
-            if (t.ld != P.n || r0 + t.rows > P.m || c0 + t.cols > P.n) {
-                snprintf(msg, sizeof msg, "%s: A term rows %lld+%d cols %lld+%d outside %lldx%lld", what,
-                         (long long)r0, t.rows, (long long)c0, t.cols, (long long)P.m, (long long)P.n);
+        if (t.buf == BUF_A || t.buf == BUF_B) {
+            const int64_t w = t.buf == BUF_A ? P.n : P.r;
+            const int64_t r0 = w ? t.off / w : 0, c0 = w ? t.off % w : 0;
+            if ((t.buf == BUF_B && !P.gemm) || t.ld != w || r0 + t.rows > P.m || c0 + t.cols > w) {
+                snprintf(msg, sizeof msg, "%s: input term rows %lld+%d cols %lld+%d outside %lldx%lld", what,
+                         (long long)r0, t.rows, (long long)c0, t.cols, (long long)P.m, (long long)w);
                 return false;
             }
         } else {
@@ -535,16 +560,27 @@ ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_
         }
         return true;
     };
-    const bool cover = n <= 4096;
-    std::vector<uint8_t> hits(cover ? (size_t)(n * (n + 1) / 2) : 0, 0);
+    const int64_t n_out = P.gemm ? P.n * P.r : n * (n + 1) / 2;
+    const bool cover = n_out <= (int64_t(1) << 24);
+    std::vector<uint8_t> hits(cover ? (size_t)n_out : 0, 0);
     auto mark = [&](int64_t i, int64_t j) -> bool {
-        if (i < 0 || j < i || j >= n) return false;
+        int64_t k;
+        if (P.gemm) {
+            if (i < 0 || j < 0 || i >= P.n || j >= P.r) return false;
+            k = i * P.r + j;
+        } else {
+            if (i < 0 || j < i || j >= n) return false;
+            k = i * n - i * (i - 1) / 2 + (j - i);
+        }
         if (cover) {
-            uint8_t& h = hits[(size_t)(i * n - i * (i - 1) / 2 + (j - i))];
+            uint8_t& h = hits[(size_t)k];
             if (h) return false;
             h = 1;
         }
         return true;
+    };
+    auto kind_ok = [&](int8_t kind) {
+        return P.gemm ? (kind == OUT_DENSE || kind == OUT_CDENSE) : (kind != OUT_CDENSE);
     };
     for (const LeafProduct& lp : P.products) {
         for (int t = 0; t < lp.nx; ++t)
@@ -553,7 +589,15 @@ ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_
             if (!term_ok(P.terms[lp.y0 + t], "leaf Y")) return fail(ATA_EINVAL, msg);
         if (lp.nx > kMaxTerms || lp.ny > kMaxTerms) return fail(ATA_EINVAL, "too many fused terms");
         if (lp.out_rows > lp.p || lp.out_cols > lp.r) return fail(ATA_EINVAL, "leaf extent beyond its product");
-        if (lp.out_kind == OUT_DENSE) {
+        if (!kind_ok(lp.out_kind)) return fail(ATA_EINVAL, "leaf output kind does not match the plan");
+        if (lp.out_kind == OUT_CDENSE) {
+            // planned with ld r and offset i0 * r + j0
+            const int64_t i0 = lp.out_off / P.r, j0 = lp.out_off % P.r;
+            if (lp.out_ld != P.r) return fail(ATA_EINVAL, "leaf C output with a wrong leading dimension");
+            for (int64_t i = 0; i < lp.out_rows; ++i)
+                for (int64_t j = 0; j < lp.out_cols; ++j)
+                    if (!mark(i0 + i, j0 + j)) return fail(ATA_EINVAL, "leaf writes C outside or twice");
+        } else if (lp.out_kind == OUT_DENSE) {
             const int64_t end = (lp.out_off + (int64_t)(lp.out_rows - 1) * lp.out_ld + lp.out_cols) * 8;
             if (lp.out_cols > lp.out_ld || end > ws) return fail(ATA_EINVAL, "leaf dense output beyond workspace");
         } else {
@@ -584,7 +628,14 @@ ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_
     for (auto& lv : P.combine_levels)
         for (const CombineTask& ct : lv) {
             if ((ct.m_off + 7LL * ct.p1 * ct.r1) * 8 > ws) return fail(ATA_EINVAL, "combine sources beyond workspace");
-            if (ct.dst_kind == OUT_DENSE) {
+            if (!kind_ok(ct.dst_kind)) return fail(ATA_EINVAL, "combine output kind does not match the plan");
+            if (ct.dst_kind == OUT_CDENSE) {
+                const int64_t i0 = ct.dst_off / P.r, j0 = ct.dst_off % P.r;
+                if (ct.dst_ld != P.r) return fail(ATA_EINVAL, "combine C output with a wrong leading dimension");
+                for (int64_t i = 0; i < ct.p; ++i)
+                    for (int64_t j = 0; j < ct.r; ++j)
+                        if (!mark(i0 + i, j0 + j)) return fail(ATA_EINVAL, "combine writes C outside or twice");
+            } else if (ct.dst_kind == OUT_DENSE) {
                 if ((ct.dst_off + (int64_t)(ct.p - 1) * ct.dst_ld + ct.r) * 8 > ws || ct.r > ct.dst_ld)
                     return fail(ATA_EINVAL, "combine output beyond workspace");
             } else {
@@ -603,20 +654,19 @@ ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_
     return ATA_OK;
 }
 
-ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
-    if (!out || !opts) return fail(ATA_EINVAL, "NULL argument");
-    *out = nullptr;
-    PlanOptions o;
-    ata_status st = make_options(m, n, dtype, *opts, &o);
+// Options (opts may be NULL for the defaults), then the autotuned cutoff.
+ata_status resolve_options(int64_t m, int64_t n, int64_t r, ata_dtype dtype, const ata_plan_options* opts,
+                           PlanOptions* o) {
+    const ata_plan_options u = opts ? *opts : default_opts(0, ATA_STRASSEN);
+    ata_status st = make_options(m, n, dtype, u, o);
     if (st != ATA_OK) return st;
-    if (opts->cutoff == 0) {
-        st = autotune_cutoff(m, n, dtype, o.variant, &o);
-        if (st != ATA_OK) return st;
-    }
-    std::unique_ptr<ata_plan_s> p(new ata_plan_s());
-    std::string err;
-    if (!build_plan(m, n, o, &p->plan, &err)) return fail(ATA_EINVAL, err);
-    st = check_terms(p->plan);
+    if (u.cutoff == 0) return autotune_cutoff(m, n, dtype, o->variant, o, r);
+    return ATA_OK;
+}
+
+// Allocates the workspace and tables of a built plan.
+ata_status finish_create(std::unique_ptr<ata_plan_s>& p, ata_dtype dtype) {
+    ata_status st = check_terms(p->plan);
     if (st != ATA_OK) return st;
     if (!leaf_supported(p->plan.leaf)) return fail(ATA_EUNSUPPORTED, "leaf kind not built into this library");
     p->id = g_plan_ids.fetch_add(1);
@@ -634,7 +684,105 @@ ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype d
             return fail(ATA_ENOMEM, "workspace: cudaMalloc of " + std::to_string(p->plan.ws_bytes) + " bytes failed");
         }
     }
-    st = rebuild_tables(p.get(), n);
+    return p->plan.gemm ? rebuild_tables(p.get(), p->plan.n, p->plan.r, p->plan.r) : rebuild_tables(p.get(), p->plan.n);
+}
+
+}  // namespace
+
+extern "C" {
+
+ata_status ata_plan_check(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
+    if (!opts) return fail(ATA_EINVAL, "NULL argument");
+    PlanOptions o;
+    ata_status st = resolve_options(m, n, -1, dtype, opts, &o);
+    if (st != ATA_OK) return st;
+    Plan P;
+    std::string err;
+    if (!build_plan(m, n, o, &P, &err)) return fail(ATA_EINVAL, err);
+    return check_plan_tables(P);
+}
+
+ata_status ata_gemm_plan_check(int64_t m, int64_t p, int64_t r, ata_dtype dtype, const ata_plan_options* opts) {
+    if (r < 0) return fail(ATA_EINVAL, "r must be >= 0");
+    PlanOptions o;
+    ata_status st = resolve_options(m, p, r, dtype, opts, &o);
+    if (st != ATA_OK) return st;
+    Plan P;
+    std::string err;
+    if (!build_gemm_plan(m, p, r, o, &P, &err)) return fail(ATA_EINVAL, err);
+    return check_plan_tables(P);
+}
+
+ata_status ata_gemm_query(int64_t m, int64_t p, int64_t r, ata_dtype dtype, const ata_plan_options* opts,
+                          ata_plan_info* out) {
+    if (!out) return fail(ATA_EINVAL, "NULL argument");
+    if (r < 0) return fail(ATA_EINVAL, "r must be >= 0");
+    PlanOptions o;
+    ata_status st = resolve_options(m, p, r, dtype, opts, &o);
+    if (st != ATA_OK) return st;
+    Plan P;
+    std::string err;
+    if (!build_gemm_plan(m, p, r, o, &P, &err)) return fail(ATA_EINVAL, err);
+    fill_info(P, dtype, out);
+    return ATA_OK;
+}
+
+ata_status ata_gemm_plan_create(ata_plan* out, int64_t m, int64_t p, int64_t r, ata_dtype dtype,
+                                const ata_plan_options* opts) {
+    if (!out) return fail(ATA_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (r < 0) return fail(ATA_EINVAL, "r must be >= 0");
+    PlanOptions o;
+    ata_status st = resolve_options(m, p, r, dtype, opts, &o);
+    if (st != ATA_OK) return st;
+    std::unique_ptr<ata_plan_s> pl(new ata_plan_s());
+    std::string err;
+    if (!build_gemm_plan(m, p, r, o, &pl->plan, &err)) return fail(ATA_EINVAL, err);
+    st = finish_create(pl, dtype);
+    if (st != ATA_OK) return st;
+    *out = pl.release();
+    return ATA_OK;
+}
+
+ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx, const void* Y, int64_t ldy, double* C,
+                       int64_t ldc, void* stream) {
+    if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    if (!plan->plan.gemm) return fail(ATA_EINVAL, "an A^t A plan: use ata_execute");
+    const int64_t m = plan->plan.m, p = plan->plan.n, r = plan->plan.r;
+    if (ldx < p || ldx < 1) return fail(ATA_EINVAL, "ldx must be >= max(p, 1)");
+    if (ldy < r || ldy < 1) return fail(ATA_EINVAL, "ldy must be >= max(r, 1)");
+    if (ldc < r || ldc < 1) return fail(ATA_EINVAL, "ldc must be >= max(r, 1)");
+    if (m > 0 && p > 0 && r > 0 && (!X || !Y)) return fail(ATA_EINVAL, "X or Y is NULL");
+    if (p > 0 && r > 0 && !C) return fail(ATA_EINVAL, "C is NULL");
+    ata_status st = check_ptr(X, elem_bytes(plan->dtype), "X");
+    if (st == ATA_OK) st = check_ptr(Y, elem_bytes(plan->dtype), "Y");
+    if (st == ATA_OK) st = check_ptr(C, 8, "C");
+    if (st != ATA_OK) return st;
+    if (p == 0 || r == 0) return ATA_OK;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (ldx != plan->lda || ldy != plan->ldb || ldc != plan->ldc) {
+        ATA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+        st = rebuild_tables(plan, ldx, ldy, ldc);
+        if (st != ATA_OK) return st;
+    }
+    Bind b = make_bind(plan, X, ldx, C);
+    b.B = Y;
+    b.b_elems = m > 0 ? (m - 1) * ldy + r : 0;
+    b.c_elems = (p - 1) * ldc + r;
+    return launch_via_graph(plan->tables, &b, 1, &plan->graph, static_cast<cudaStream_t>(stream));
+}
+
+
+ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
+    if (!out || !opts) return fail(ATA_EINVAL, "NULL argument");
+    *out = nullptr;
+    PlanOptions o;
+    ata_status st = resolve_options(m, n, -1, dtype, opts, &o);
+    if (st != ATA_OK) return st;
+    std::unique_ptr<ata_plan_s> p(new ata_plan_s());
+    std::string err;
+    if (!build_plan(m, n, o, &p->plan, &err)) return fail(ATA_EINVAL, err);
+    st = finish_create(p, dtype);
     if (st != ATA_OK) return st;
     *out = p.release();
     return ATA_OK;
@@ -668,6 +816,7 @@ ata_status ata_plan_workspace_size(ata_plan plan, size_t* bytes) {
 
 ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_packed, void* stream) {
     if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan: use ata_gemm_tn");
     const int64_t m = plan->plan.m, n = plan->plan.n;
     if (lda < n || lda < 1) return fail(ATA_EINVAL, "lda must be >= max(n, 1)");
     if (m > 0 && n > 0 && !A) return fail(ATA_EINVAL, "A is NULL");
@@ -690,6 +839,7 @@ ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_pack
 
 ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, double* C_host, void* stream) {
     if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan: use ata_gemm_tn");
     const int64_t m = plan->plan.m, n = plan->plan.n;
     const int es = elem_bytes(plan->dtype);
     if (lda < n || lda < 1) return fail(ATA_EINVAL, "lda must be >= max(n, 1)");

@@ -100,7 +100,9 @@ extern thread_local std::string g_last_error;
 ata_status fail(ata_status s, const std::string& msg);
 ata_status cuda_fail(cudaError_t e, const char* what);
 
-void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h);
+// lda: leading dimension of A (X of a general product); ldb, ldc: of Y and of
+// the dense C of a general product (unused for A^t A plans).
+void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h, int64_t ldb = 0, int64_t ldc = 0);
 void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt);
 ata_status upload_tables(const HostTables& h, DeviceTables* d);
 ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cudaStream_t s,
@@ -119,7 +121,8 @@ int tc_rows_for(const Plan& P);
 // Planner defaults and the autotuner.
 int default_cutoff(int64_t m, int64_t n, ata_dtype dtype);
 int default_fuse_levels(ata_dtype dtype, int variant);
-ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o);
+// r >= 0 tunes the general product X^t Y (X: m x n, Y: m x r) instead.
+ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o, int64_t r = -1);
 
 // Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
 const Plan& plan_of(ata_plan p);

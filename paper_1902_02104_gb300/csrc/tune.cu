@@ -94,7 +94,7 @@ double estimate_products(int64_t m, int64_t n, int cutoff) {
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int64_t, int, int>, int> g_tuned;
+std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int>, int> g_tuned;
 
 }  // namespace
 
@@ -115,8 +115,8 @@ int default_cutoff(int64_t m, int64_t n, ata_dtype dtype) {
     }
 }
 
-ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o) {
-    const auto key = std::make_tuple(m, n, (int)dtype, variant);
+ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o, int64_t r) {
+    const auto key = std::make_tuple(m, n, r, (int)dtype, variant, o->fuse_levels, o->max_levels, (int)o->cta_pair);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -129,13 +129,14 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
     double best = 1e300;
     int best_c = o->cutoff;
     for (int c : cands) {
-        if (estimate_products(m, n, c) > kMaxLeafProducts) continue;
+        if (r < 0 && estimate_products(m, n, c) > kMaxLeafProducts) continue;
         if (dtype != ATA_F64 && c < 256) continue;  // tensor-core tiles are 128 x 128
         PlanOptions t = *o;
         t.cutoff = c;
         Plan P;
         std::string err;
-        if (!build_plan(m, n, t, &P, &err)) continue;
+        if (!(r < 0 ? build_plan(m, n, t, &P, &err) : build_gemm_plan(m, n, r, t, &P, &err))) continue;
+        if ((int64_t)P.products.size() > kMaxLeafProducts) continue;
         if (P.ws_bytes > kWorkspaceCap) continue;
         const double tm = model_time(P, dtype);
         if (tm < best) {

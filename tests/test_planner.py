@@ -74,6 +74,13 @@ def test_invalid_arguments(bad):
     assert e.value.status == ata.ATA_EINVAL
 
 
+def test_invalid_cta_pair_option():
+    for bad in (-2, 2):
+        with pytest.raises(ata.AtaError) as e:
+            q(100, 100, 64, ata.ATA_F32_BF16X3, cta_pair=bad)
+        assert e.value.status == ata.ATA_EINVAL
+
+
 def test_invalid_dtype_and_variant():
     with pytest.raises(ata.AtaError):
         ata.ata_plan_query(10, 10, 9, 64)
@@ -96,12 +103,15 @@ def _upper_tiles(rows, tm, tn):
 
 @pytest.mark.parametrize("n", [100, 129, 256, 300, 511, 640, 1000, 1023, 1500, 2047])
 def test_leaf_tile_shape_single_syrk_leaf(n):
-    # one diagonal leaf (n <= cutoff): 128-row tiles unless every X operand is
-    # wider than one tile and 256-row tiles cover at most 1/8 more area
+    # one diagonal leaf (n <= cutoff): 128-row tiles unless the CTA-pair
+    # option is set, every X operand is wider than one tile and 256-row tiles
+    # cover at most 1/8 more area
     for dtype in (ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI):
-        i = q(300, n, 4096, dtype)
         t128 = _upper_tiles(n, 128, 128)
         t256 = _upper_tiles(n, 256, 128)
+        d = q(300, n, 4096, dtype)  # default: single-CTA 128 x 128 tiles
+        assert (d["leaf_tile_rows"], d["leaf_tile_cols"], d["n_leaf_tiles"]) == (128, 128, t128)
+        i = q(300, n, 4096, dtype, cta_pair=1)
         pair = n > 128 and t256 * 256 <= 1.125 * t128 * 128
         assert i["leaf_tile_cols"] == 128
         assert i["leaf_tile_rows"] == (256 if pair else 128), (n, t128, t256)

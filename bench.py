@@ -1,13 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of C = A^t A on one GB300 (or N replicas under torchrun).
 
-Default workload: plain FP64 ATA at the paper's scale, A 10000 x 10000 with
-i.i.d. N(0, 1) entries from seed 1, cutoff chosen by the planner's autotuner,
-packed upper-triangle FP64 output.  A step is one ata_execute (one replay of
-the plan's CUDA graph: operand splits, the persistent leaf launch, Strassen
-combines) over the resident input.  The metric is effective TFLOP/s =
-2 m n^2 / t (m n^2 classical FMAs), at the componentwise error reported in
-the line.
+Default workload: ATA at the paper's scale with FP64 accuracy, A 10000 x 10000
+FP64 with i.i.d. N(0, 1) entries from seed 1, leaves emulating FP64 on the
+bf16 tensor cores (6 slices), cutoff chosen by the planner's autotuner, packed
+upper-triangle FP64 output, componentwise error against the oracle <= 1e-11;
+the plain FP64 path on the same input is timed beside it.  A step is one
+ata_execute (one replay of the plan's CUDA graph: operand splits, operand
+preparation, the persistent leaf launch, Strassen combines) over the resident
+input.  The metric is effective TFLOP/s = 2 m n^2 / t (m n^2 classical FMAs),
+at the error reported in the line.  Other workloads: --workload NAME (the
+plain FP64 and precision forms, batched, serving, and the general product
+C = X^t Y through ata_gemm_tn, metric 2 m p r / t).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME]
@@ -58,6 +62,14 @@ PAIRS = {"f64": 1, "bf16x3": 6, "tf32": 1, "ozaki": 21}
 TOLERANCE = {"f64": ("componentwise", 1e-11), "ozaki": ("componentwise", 1e-11),
              "bf16x3": ("normwise", 1e-6), "tf32": ("normwise", 1e-3)}
 DEFAULT_WORKLOAD = "ata_ozaki_10000x10000"
+# general product C = X^t Y (X: m x p, Y: m x r): the top C_12 product of a
+# 10000^2 A^t A, and the precision form's shape
+GEMM_WORKLOADS = {
+    # name: (m, p, r, leaf mode, generator, seed, cutoff (0 = autotune))
+    "gemm_tn_ozaki_10000x5000x5000": (10000, 5000, 5000, "ozaki", "normal", 1, 0),
+    "gemm_tn_f64_10000x5000x5000": (10000, 5000, 5000, "f64", "normal", 1, 0),
+    "gemm_tn_bf16x3_16384x4096x4096": (16384, 4096, 4096, "bf16x3", "scaled_cols", 2, 0),
+}
 # workloads run by their own drivers (not single products)
 EXTRA_WORKLOADS = ["batched_bf16x3", "batched_f64", "serving_bf16x3", "serving_ozaki"]
 
@@ -215,17 +227,23 @@ def barrier(world):
 
 def cpu_oracle_sample(A, budget_s=15.0):
     """Times the oracle on leading rows of the packed triangle for about
-    budget_s seconds and extrapolates to the whole product."""
+    budget_s seconds of multiply-adds and extrapolates to the whole product.
+    Every call of the row routine first copies A into column-major order; that
+    fixed cost (timed on a one-row call) is taken off each measurement, so the
+    extrapolation scales only the multiply-adds."""
     import oracle
     m, n = A.shape
     total = m * n * (n + 1) / 2
-    # calibrate on a few rows
-    rows = max(1, min(n, 16))
     t0 = time.perf_counter()
-    oracle.ata_rows(A, 0, rows)
-    dt = time.perf_counter() - t0
-    done = m * sum(n - i for i in range(rows))
-    rate = done / max(dt, 1e-6)
+    oracle.ata_rows(A, 0, 1)
+    t_fixed = time.perf_counter() - t0  # the copy (and one row)
+    # calibrate on a few more rows
+    rows = max(2, min(n, 64))
+    t0 = time.perf_counter()
+    oracle.ata_rows(A, 1, rows)
+    dt = max(time.perf_counter() - t0 - t_fixed, 1e-6)
+    done = m * sum(n - i for i in range(1, rows))
+    rate = done / dt
     # grow to the budget
     want = rate * budget_s
     r1 = rows
@@ -235,11 +253,11 @@ def cpu_oracle_sample(A, budget_s=15.0):
         r1 += 1
     t0 = time.perf_counter()
     oracle.ata_rows(A, rows, r1)
-    dt = time.perf_counter() - t0
+    dt = max(time.perf_counter() - t0 - t_fixed, 1e-6)
     done = m * sum(n - i for i in range(rows, r1))
     t_full = dt * total / max(done, 1)
     return {"t_full_s": t_full, "rows": (rows, r1), "sample_s": dt, "cores": oracle.num_threads(),
-            "frac": done / total}
+            "frac": done / total, "fixed_s": t_fixed}
 
 
 def run_reference(args):
@@ -617,13 +635,145 @@ def run_serving(args, mode):
     return 0
 
 
+def run_gemm(args):
+    """The general product C = X^t Y through ata_gemm_tn (X: m x p, Y: m x r,
+    C: p x r dense FP64).  A step is one call over resident X and Y; the
+    metric is effective TFLOP/s = 2 m p r / t."""
+    import torch
+
+    import oracle
+    import paper_1902_02104_gb300 as ata
+    from paper_1902_02104_gb300 import inputs
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    m, p, r, mode, gen, seed, cutoff = GEMM_WORKLOADS[name]
+    if args.cutoff is not None:
+        cutoff = args.cutoff
+    dt = np.float64 if mode in ("f64", "ozaki") else np.float32
+    X_np = getattr(inputs, gen)(m, p, seed=seed).astype(dt)
+    Y_np = getattr(inputs, gen)(m, r, seed=seed + 1).astype(dt)
+    plan = ata.GemmPlan(m, p, r, MODE_CODES[mode], cutoff)
+    info = plan.info
+    X = torch.from_numpy(X_np).to(dev)
+    Y = torch.from_numpy(Y_np).to(dev)
+    C = torch.empty((p, r), dtype=torch.float64, device=dev)
+    plan.enable_stage_timing(True)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan(X, Y, C)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_smi_index(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    leaf_ms, stage = [], {"split": [], "prep": [], "leaf": [], "combine": []}
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan(X, Y, C)
+        stream.synchronize()
+        st = plan.stage_times()
+        for k in stage:
+            stage[k].append(st[k + "_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = max_over_ranks(torch, e0.elapsed_time(e1) / args.steps, world)
+    # accuracy on sampled entries
+    rng = np.random.default_rng(123)
+    I = rng.integers(0, p, 2000)
+    J = rng.integers(0, r, 2000)
+    got = C[torch.from_numpy(I).to(dev), torch.from_numpy(J).to(dev)].cpu().numpy()
+    ref = oracle.gemm_entries(X_np, Y_np, I, J)
+    kind, tol = TOLERANCE[mode]
+    if kind == "componentwise":
+        G = oracle.gemm_entries(X_np, Y_np, I, J, absval=True)
+        err = float(np.max(np.abs(got - ref) / G))
+    else:
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        kind = "normwise_sampled_entries"
+    # end to end: pinned host X, Y in, C out, through the same call
+    Xh = torch.from_numpy(X_np).pin_memory()
+    Yh = torch.from_numpy(Y_np).pin_memory()
+    Ch = torch.empty((p, r), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Xd = Xh.to(dev, non_blocking=True)
+        Yd = Yh.to(dev, non_blocking=True)
+        plan(Xd, Yd, C)
+        Ch.copy_(C, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / e2e_steps, world)
+    eff = 2.0 * m * p * r
+    leaf_s = statistics.mean(stage["leaf"]) / 1e3
+    leaf_flops = 2.0 * info["mults"] * PAIRS[mode]
+    if mode == "f64":
+        kern, bound, peak, peak_src = "leaf_f64_kernel", "alu", FP64_ALU_PEAK_TFLOPS, \
+            "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"
+    else:
+        kern, bound = "tc_gemm_kernel", "tensor"
+        peak, peak_src = tensor_peak(mode)
+    line = _line_common(args, world, "effective TFLOP/s (2 m p r) of C = X^t Y", world * eff / (ms / 1e3) / 1e12,
+                        "TFLOP/s", ms, mode,
+                        {"workload": name, "m": m, "p": p, "r": r, "leaf": mode, "generator": f"{gen}(seed={seed})",
+                         "cutoff": info["cutoff"], "strassen_levels": info["max_strassen_levels"],
+                         "parallelism": f"replicas{world}",
+                         "l2": "inputs larger than L2 (X is %d MB)" % (X_np.nbytes >> 20)})
+    line["error"] = {kind: err, "tolerance": tol, "samples": 2000, "device_status": plan.device_status()}
+    line["stages_ms"] = {k: statistics.mean(v) for k, v in stage.items()}
+    line["roofline"] = {"bound": bound, "achieved": leaf_flops / leaf_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": leaf_flops / leaf_s / 1e12 / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": kern, "flops_per_launch": leaf_flops}
+    line["e2e"] = {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s",
+                   "h2d_bytes_per_step": int(X_np.nbytes + Y_np.nbytes), "d2h_bytes_per_step": int(p * r * 8)}
+    line["gpu_launches"] = int(args.steps * info["n_launches"])
+    line["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample of entries (about --cpu-budget
+        # seconds), extrapolated to all p r entries
+        srng = np.random.default_rng(7)
+        cnt = 2048
+        Is, Js = srng.integers(0, p, cnt), srng.integers(0, r, cnt)
+        t0 = time.perf_counter()
+        oracle.gemm_entries(X_np, Y_np, Is, Js)
+        per = (time.perf_counter() - t0) / cnt
+        cnt = int(min(p * r, max(cnt, args.cpu_budget / max(per, 1e-9))))
+        Is, Js = srng.integers(0, p, cnt), srng.integers(0, r, cnt)
+        t0 = time.perf_counter()
+        oracle.gemm_entries(X_np, Y_np, Is, Js)
+        dt_s = time.perf_counter() - t0
+        t_full = dt_s * p * r / cnt
+        line["cpu_baseline"] = {"value": eff / t_full / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"{cnt} sampled entries ({dt_s:.1f} s), extrapolated "
+                                                            f"to all {p * r} entries"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + EXTRA_WORKLOADS, default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(GEMM_WORKLOADS) + EXTRA_WORKLOADS,
+                    default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
@@ -634,7 +784,13 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if args.workload not in WORKLOADS:
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the A^t A oracle on the "
+                                                                  "A^t A workloads only"}))
+            return 0
         return run_reference(args)
+    if args.workload in GEMM_WORKLOADS:
+        return run_gemm(args)
     if args.workload.startswith("batched_"):
         return run_batched(args, args.workload.split("_", 1)[1])
     if args.workload.startswith("serving_"):

@@ -1,5 +1,6 @@
 /*
- * Oracle for C = A^t A (test infrastructure only).
+ * Oracle for C = A^t A and for the general product C = X^t Y (test
+ * infrastructure only).
  *
  * This file is part of the test oracle.  Only the tests, the smoke check and
  * the CPU-baseline leg of the benchmark may load it; the product path never
@@ -142,6 +143,74 @@ int oracle_ata_rows(const double* A, int64_t m, int64_t n, int64_t lda,
         }
     }
     free(At);
+    return 0;
+}
+
+/* General product C = X^t Y (the HASA step of Section 4.2.2 on two
+ * operands; the off-diagonal block C_12 of the recursion is one such
+ * product): X is m x p (ldx >= p), Y is m x r (ldy >= r), both row-major;
+ * C is p x r row-major with ldc >= r,
+ *
+ *     C[i][j] = sum_{k=0}^{m-1} X[k][i] * Y[k][j],
+ *
+ * k ascending, one accumulator per entry, the same arithmetic as the
+ * functions above (with X = Y = A the entries j >= i are bitwise those of
+ * oracle_ata_packed).  If absval != 0, computes |X|^t |Y| (the denominator
+ * of the componentwise error).  Returns 0, -1 on bad arguments, -2 if out of
+ * memory. */
+int oracle_gemm_tn(const double* X, int64_t m, int64_t p, int64_t ldx,
+                   const double* Y, int64_t r, int64_t ldy,
+                   double* C, int64_t ldc, int absval)
+{
+    if (m < 0 || p < 0 || r < 0 || ldx < p || ldy < r || ldc < r) return -1;
+    if (p == 0 || r == 0) return 0;
+    if (!C || (m > 0 && (!X || !Y))) return -1;
+    double* Xt = column_major_copy(X, m, p, ldx, absval);
+    double* Yt = column_major_copy(Y, m, r, ldy, absval);
+    if (!Xt || !Yt) {
+        free(Xt);
+        free(Yt);
+        return -2;
+    }
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (i = 0; i < p; ++i) {
+        const double* xi = Xt + i * m;
+        for (int64_t j = 0; j < r; ++j) {
+            const double* yj = Yt + j * m;
+            double acc = 0.0;
+            for (int64_t k = 0; k < m; ++k) acc = acc + xi[k] * yj[k];
+            C[i * ldc + j] = acc;
+        }
+    }
+    free(Xt);
+    free(Yt);
+    return 0;
+}
+
+/* Selected entries of X^t Y (or |X|^t |Y|): out[t] = C[I[t]][J[t]], the same
+ * arithmetic as oracle_gemm_tn (sampled parity at sizes too large for the
+ * full product on the host). */
+int oracle_gemm_entries(const double* X, int64_t m, int64_t p, int64_t ldx,
+                        const double* Y, int64_t r, int64_t ldy,
+                        const int64_t* I, const int64_t* J, int64_t count,
+                        int absval, double* out)
+{
+    if (m < 0 || p < 0 || r < 0 || ldx < p || ldy < r || count < 0) return -1;
+    if (count > 0 && (!I || !J || !out)) return -1;
+    for (int64_t t = 0; t < count; ++t)
+        if (I[t] < 0 || I[t] >= p || J[t] < 0 || J[t] >= r) return -1;
+    int64_t t;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (t = 0; t < count; ++t) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < m; ++k) {
+            double a = X[k * ldx + I[t]], b = Y[k * ldy + J[t]];
+            if (absval) { a = fabs(a); b = fabs(b); }
+            acc = acc + a * b;
+        }
+        out[t] = acc;
+    }
     return 0;
 }
 

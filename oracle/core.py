@@ -47,8 +47,11 @@ def _load():
             lib.oracle_abs_gram_packed.argtypes = [dp, i64, i64, i64, dp]
             lib.oracle_ata_entries.argtypes = [dp, i64, i64, i64, dp, dp, i64, ctypes.c_int, dp]
             lib.oracle_ata_rows.argtypes = [dp, i64, i64, i64, i64, i64, dp]
+            lib.oracle_gemm_tn.argtypes = [dp, i64, i64, i64, dp, i64, i64, dp, i64, ctypes.c_int]
+            lib.oracle_gemm_entries.argtypes = [dp, i64, i64, i64, dp, i64, i64, dp, dp, i64, ctypes.c_int, dp]
             for f in (lib.oracle_ata_packed, lib.oracle_abs_gram_packed,
-                      lib.oracle_ata_entries, lib.oracle_ata_rows):
+                      lib.oracle_ata_entries, lib.oracle_ata_rows, lib.oracle_gemm_tn,
+                      lib.oracle_gemm_entries):
                 f.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -125,6 +128,36 @@ def ata_rows(A, i0: int, i1: int) -> np.ndarray:
         packed_size(n) - int(packed_index(i0, i0, n)) if i0 < n else 0
     out = np.empty(max(cnt, 0), dtype=np.float64)
     _check(_load().oracle_ata_rows(A.ctypes.data, m, n, n, i0, i1, out.ctypes.data), "oracle_ata_rows")
+    return out
+
+
+def gemm_tn(X, Y, absval: bool = False) -> np.ndarray:
+    """C = X^t Y (p x r, FP64) for X: m x p and Y: m x r, k ascending, one
+    accumulator per entry; with absval, |X|^t |Y|."""
+    X = _as_f64(X)
+    Y = _as_f64(Y)
+    if X.shape[0] != Y.shape[0]:
+        raise ValueError("X and Y must have the same number of rows")
+    m, p = X.shape
+    r = Y.shape[1]
+    C = np.zeros((p, r), dtype=np.float64)
+    _check(_load().oracle_gemm_tn(X.ctypes.data, m, p, p, Y.ctypes.data, r, r, C.ctypes.data, r, int(absval)),
+           "oracle_gemm_tn")
+    return C
+
+
+def gemm_entries(X, Y, I, J, absval: bool = False) -> np.ndarray:
+    """Entries (I[t], J[t]) of X^t Y (or |X|^t|Y|), bitwise equal to the same
+    entries of :func:`gemm_tn`."""
+    X = _as_f64(X)
+    Y = _as_f64(Y)
+    m, p = X.shape
+    r = Y.shape[1]
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    out = np.empty(I.size, dtype=np.float64)
+    _check(_load().oracle_gemm_entries(X.ctypes.data, m, p, p, Y.ctypes.data, r, r, I.ctypes.data, J.ctypes.data,
+                                       I.size, int(absval), out.ctypes.data), "oracle_gemm_entries")
     return out
 
 

@@ -438,7 +438,14 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     for (auto& v : P.combine_levels) nc += v.size();
     out->n_sum_tasks = (int32_t)ns;
     out->n_combine_tasks = (int32_t)nc;
-    out->n_launches = (int32_t)(P.split_levels.size() + P.combine_levels.size() + (P.products.empty() ? 0 : 1));
+    // kernels one execution launches: a split and a combine kernel per level,
+    // then the leaf kernel, preceded for tensor-core leaves by the operand
+    // preparation (and the column maxima of the sliced modes)
+    const int leaf_kernels = P.products.empty() ? 0
+                             : P.leaf == LEAF_F64 ? 1
+                             : P.leaf == LEAF_TF32 ? 2
+                                                   : 3;
+    out->n_launches = (int32_t)(P.split_levels.size() + P.combine_levels.size() + leaf_kernels);
     out->mults = P.stats.mults;
     out->classical_mults = P.m * P.n * (P.n + 1) / 2;  // A^t A: the upper triangle
     out->adds = P.stats.adds;

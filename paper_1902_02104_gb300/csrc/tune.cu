@@ -28,15 +28,16 @@ struct Rates {
 };
 
 // Rates measured on GB300: DFMA leaves at ~90% of 1.26 TFLOP/s; tensor-core
-// leaves at ~60% of the 1.89 PFLOP/s bf16 (0.93 tf32) peak divided by the
-// part products per scalar product (6 for bf16x3, 21 for the FP64
-// emulation); Strassen sums/combines on the FP64 (0.5 Gop/s) or FP32 pipe.
+// leaves at the measured fraction of the 1.89 PFLOP/s bf16 (0.93 tf32) peak
+// (0.75 FP64 emulation, 0.68 bf16x3, 0.53 TF32) divided by the part
+// products per scalar product (21, 6, 1); Strassen sums/combines on the
+// FP64 (0.5 Gop/s) or FP32 pipe.
 Rates rates_for(ata_dtype d) {
     switch (d) {
         case ATA_F64: return {0.57e12, 0.50e12, 6.0e12};
-        case ATA_F32_BF16X3: return {1.89e15 * 0.6 / 2 / 6, 35e12, 6.0e12};
-        case ATA_F32_TF32: return {0.93e15 * 0.6 / 2, 35e12, 6.0e12};
-        case ATA_F64_OZAKI: return {1.89e15 * 0.6 / 2 / 21, 0.5e12, 6.0e12};
+        case ATA_F32_BF16X3: return {1.89e15 * 0.68 / 2 / 6, 35e12, 6.0e12};
+        case ATA_F32_TF32: return {0.93e15 * 0.53 / 2, 35e12, 6.0e12};
+        case ATA_F64_OZAKI: return {1.89e15 * 0.75 / 2 / 21, 0.5e12, 6.0e12};
     }
     return {0.6e12, 0.5e12, 6e12};
 }
@@ -61,8 +62,16 @@ double model_time(const Plan& P, ata_dtype d) {
     const Rates r = rates_for(d);
     // tensor-core leaves compute on whole tiles (128 x 128, or 256 x 128 for
     // CTA pairs)
-    double leaf = (double)P.stats.mults;
-    if (P.leaf != LEAF_F64) {
+    // FP64 leaves skip padding in 16 x 32 warp blocks (upper blocks only on
+    // diagonal leaves), so they pay for whole blocks
+    double leaf = 0;
+    if (P.leaf == LEAF_F64) {
+        for (const LeafProduct& lp : P.products) {
+            const double rb = std::ceil(lp.out_rows / 16.0), cb = std::ceil(lp.out_cols / 32.0);
+            const double blocks = lp.out_kind == OUT_SYRK ? rb * cb / 2 + std::min(rb, cb) / 2 : rb * cb;
+            leaf += blocks * 16.0 * 32.0 * lp.K;
+        }
+    } else {
         leaf = 0;
         const int tm = P.tc_tile_rows > 0 ? P.tc_tile_rows : kTcTile;
         for (const LeafProduct& lp : P.products)

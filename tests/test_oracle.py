@@ -257,3 +257,92 @@ def test_cost_constant_reading():
     n = 2.0 ** 20
     total = sum(4 ** l * (2 / 7) * (n / 2 ** l) ** lg7 for l in range(60))
     assert total / n ** lg7 == pytest.approx(2 / 3, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# General product C = X^t Y (the HASA step of Section 4.2.2 on two operands)
+
+def exact_gemm_tn(X, Y):
+    m, p = X.shape
+    r = Y.shape[1]
+    FX = [[Fraction(float(X[k, i])) for i in range(p)] for k in range(m)]
+    FY = [[Fraction(float(Y[k, j])) for j in range(r)] for k in range(m)]
+    return [[sum((FX[k][i] * FY[k][j] for k in range(m)), Fraction(0)) for j in range(r)] for i in range(p)]
+
+
+def test_gemm_brute_force_tiny_against_rationals():
+    rng = np.random.default_rng(31)
+    for m, p, r in itertools.product(range(0, 5), range(1, 5), range(1, 5)):
+        X = rng.standard_normal((m, p))
+        Y = rng.standard_normal((m, r))
+        C = oracle.gemm_tn(X, Y)
+        G = oracle.gemm_tn(X, Y, absval=True)
+        E = exact_gemm_tn(X, Y)
+        gamma = m * U / (1 - m * U)
+        for i in range(p):
+            for j in range(r):
+                assert abs(Fraction(C[i, j]) - E[i][j]) <= Fraction(gamma) * Fraction(G[i, j]), (m, p, r, i, j)
+
+
+def test_gemm_tiny_integers_equal_rationals_bitwise():
+    rng = np.random.default_rng(32)
+    for m, p, r in itertools.product(range(0, 6), range(1, 5), range(1, 5)):
+        X = rng.integers(-9, 10, size=(m, p)).astype(np.float64)
+        Y = rng.integers(-9, 10, size=(m, r)).astype(np.float64)
+        E = exact_gemm_tn(X, Y)
+        want = np.array([[float(E[i][j]) for j in range(r)] for i in range(p)]).reshape(p, r)
+        assert np.array_equal(oracle.gemm_tn(X, Y), want)
+
+
+@pytest.mark.parametrize("m,p,r", [(1, 1, 1), (7, 3, 5), (3, 7, 2), (64, 48, 80), (129, 65, 33), (1024, 37, 50)])
+def test_gemm_exact_integers_against_int64(m, p, r):
+    X = inputs.integers(m, p, seed=m + p)
+    Y = inputs.integers(m, r, seed=m + r + 1)
+    want = (X.astype(np.int64).T @ Y.astype(np.int64)).astype(np.float64)
+    assert np.array_equal(oracle.gemm_tn(X, Y), want)
+
+
+def test_gemm_with_itself_is_the_gram_bitwise():
+    # X = Y = A: the same k-ascending sums as the A^t A oracle
+    A = inputs.normal(300, 70, seed=5)
+    C = oracle.gemm_tn(A, A)
+    assert np.array_equal(C[np.triu_indices(70)], oracle.ata_packed(A))
+    G = oracle.gemm_tn(A, A, absval=True)
+    assert np.array_equal(G[np.triu_indices(70)], oracle.abs_gram_packed(A))
+
+
+def test_gemm_closed_forms():
+    # X = [I_p; 0]: C = the first p rows of Y
+    Y = inputs.normal(50, 30, seed=6)
+    X = np.zeros((50, 20))
+    X[:20, :20] = np.eye(20)
+    assert np.array_equal(oracle.gemm_tn(X, Y), Y[:20])
+    # X = a b^t, Y = a c^t (integers): X^t Y = (a.a) b c^t exactly
+    rng = np.random.default_rng(7)
+    a = rng.integers(-5, 6, size=40).astype(float)
+    b = rng.integers(-5, 6, size=9).astype(float)
+    c = rng.integers(-5, 6, size=11).astype(float)
+    assert np.array_equal(oracle.gemm_tn(np.outer(a, b), np.outer(a, c)), float(a @ a) * np.outer(b, c))
+
+
+def test_gemm_matches_strassen_restatement_on_integers():
+    rng = np.random.default_rng(8)
+    X = rng.integers(-4, 5, size=(70, 45)).astype(float)
+    Y = rng.integers(-4, 5, size=(70, 38)).astype(float)
+    for v in ("strassen", "winograd"):
+        assert np.array_equal(R.hasa(X.T, Y, 8, variant=v), oracle.gemm_tn(X, Y))
+
+
+def test_gemm_entries_and_degenerate_shapes():
+    X = inputs.normal(90, 25, seed=9)
+    Y = inputs.normal(90, 31, seed=10)
+    C = oracle.gemm_tn(X, Y)
+    I = np.array([0, 24, 3, 11])
+    J = np.array([30, 0, 3, 17])
+    assert np.array_equal(oracle.gemm_entries(X, Y, I, J), C[I, J])
+    assert np.array_equal(oracle.gemm_entries(X, Y, I, J, absval=True),
+                          oracle.gemm_tn(np.abs(X), np.abs(Y))[I, J])
+    assert np.array_equal(oracle.gemm_tn(np.zeros((0, 4)), np.zeros((0, 3))), np.zeros((4, 3)))
+    assert oracle.gemm_tn(np.zeros((5, 0)), np.zeros((5, 3))).shape == (0, 3)
+    with pytest.raises(Exception):
+        oracle.gemm_tn(np.zeros((5, 2)), np.zeros((4, 3)))

@@ -119,3 +119,41 @@ def test_leaf_tile_shape_single_syrk_leaf(n):
     f = q(300, n, 4096, ata.ATA_F64)
     assert (f["leaf_tile_rows"], f["leaf_tile_cols"]) == (64, 64)
     assert f["n_leaf_tiles"] == _upper_tiles(n, 64, 64)
+
+
+# ---------------------------------------------------------------------------
+# General product plans (X^t Y)
+
+@pytest.mark.parametrize("m,p,r,c", [(512, 384, 300, 64), (700, 333, 517, 64), (300, 129, 1000, 32),
+                                     (1030, 260, 260, 128), (100, 1, 7, 16), (64, 64, 64, 16)])
+def test_gemm_counts_match_hasa_restatement(m, p, r, c):
+    # the planner's multiplication count equals the Strassen restatement's
+    # on the same (p, q = m, r) with the same cutoff
+    cnt = R.MultCounter()
+    R.hasa(np.zeros((p, m)), np.zeros((m, r)), c, cnt)
+    i = ata.ata_gemm_query(m, p, r, ata.ATA_F64, c)
+    assert i["mults"] == cnt.mults
+    assert i["classical_mults"] == m * p * r
+    assert (i["n"], i["r"]) == (p, r)
+
+
+@pytest.mark.parametrize("dtype", [ata.ATA_F64, ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI])
+@pytest.mark.parametrize("variant", [ata.ATA_STRASSEN, ata.ATA_WINOGRAD])
+@pytest.mark.parametrize("fuse", [0, 1, 2])
+def test_gemm_plan_tables_cover_c_once(dtype, variant, fuse):
+    for m, p, r, c in [(512, 384, 300, 64), (1000, 999, 777, 128), (257, 1025, 513, 64), (90, 700, 33, 16)]:
+        ata.ata_gemm_plan_check(m, p, r, dtype, c, variant=variant, fuse_levels=fuse)
+
+
+def test_gemm_classical_when_strassen_disabled():
+    i = ata.ata_gemm_query(2000, 1500, 1700, ata.ATA_F64, 64, max_strassen_levels=0)
+    assert i["max_strassen_levels"] == 0 and i["mults"] == 2000 * 1500 * 1700
+
+
+def test_gemm_invalid_arguments():
+    for args in [(-1, 3, 3), (3, -1, 3), (3, 3, -1)]:
+        with pytest.raises(ata.AtaError) as e:
+            ata.ata_gemm_query(*args, ata.ATA_F64, 64)
+        assert e.value.status == ata.ATA_EINVAL
+    with pytest.raises(ata.AtaError):
+        ata.ata_gemm_query(10, 10, 10, ata.ATA_F64, 8)

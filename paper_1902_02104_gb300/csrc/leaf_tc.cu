@@ -524,8 +524,18 @@ __device__ __forceinline__ void load_operand_tile(const BindSet<NB>& bs, const T
 
 // Column maxima of |operand| (sliced modes): atomicMax on the FP64 bit
 // pattern (positive doubles order like their bits; Inf and NaN order above
-// every finite value).  Block: a 64 (K) x 64 (column) tile, reduced in
-// registers over a thread's rows, then across the threads of a column.
+// every finite value).  Block: rows [k0, k1) (up to kColSpan) of a 64-column
+// strip, read two 64-row tiles at a time (16 loads in flight per thread),
+// reduced in registers over a thread's rows, then across the threads of a
+// column; one atomic per column and block.
+template <typename TS>
+__device__ __forceinline__ unsigned long long abs_bits(TS x) {
+    if constexpr (sizeof(TS) == 8)
+        return (unsigned long long)__double_as_longlong((double)x) & 0x7FFFFFFFFFFFFFFFull;
+    else
+        return __float_as_uint((float)x) & 0x7FFFFFFFu;
+}
+
 template <int NB, typename TS>
 __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ BindSet<NB> bs,
                                                         const LeafProduct* __restrict__ prods,
@@ -538,45 +548,50 @@ __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ 
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
-    TileRegs<TS> R;
-    load_operand_regs<TS>(bs, terms, t0, nt, lp.K, tk.k0, tk.c0, R);
-    // magnitudes compared as bit patterns (integer operations only)
+    unsigned long long m[TR::VEC];
+#pragma unroll
+    for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
+    for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
+        TileRegs<TS> R0, R1;
+        load_operand_regs<TS>(bs, terms, t0, nt, tk.k1, k, tk.c0, R0);
+        load_operand_regs<TS>(bs, terms, t0, nt, tk.k1, k + PT, tk.c0, R1);
+        // magnitudes compared as bit patterns (integer operations only)
+#pragma unroll
+        for (int j = 0; j < TR::VEC; ++j)
+#pragma unroll
+            for (int p = 0; p < TR::NPASS; ++p) {
+                const unsigned long long b0 = abs_bits(R0.v[p][j]), b1 = abs_bits(R1.v[p][j]);
+                const unsigned long long b = b0 > b1 ? b0 : b1;
+                m[j] = b > m[j] ? b : m[j];
+            }
+    }
     const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
     const int r0 = threadIdx.x / TR::VPR;
 #pragma unroll
-    for (int j = 0; j < TR::VEC; ++j) {
-        unsigned long long m = 0;
-#pragma unroll
-        for (int p = 0; p < TR::NPASS; ++p) {
-            unsigned long long b;
-            if constexpr (sizeof(TS) == 8)
-                b = (unsigned long long)__double_as_longlong((double)R.v[p][j]) & 0x7FFFFFFFFFFFFFFFull;
-            else
-                b = __float_as_uint((float)R.v[p][j]) & 0x7FFFFFFFu;
-            m = b > m ? b : m;
-        }
-        red[r0][vc + j] = m;
-    }
+    for (int j = 0; j < TR::VEC; ++j) red[r0][vc + j] = m[j];
     __syncthreads();
     if (threadIdx.x < PT) {
         const int col = threadIdx.x;
-        unsigned long long m = red[0][col];
+        unsigned long long mx = red[0][col];
 #pragma unroll
-        for (int i = 1; i < NRED; ++i) m = red[i][col] > m ? red[i][col] : m;
-        if (m != 0) {
-            if constexpr (sizeof(TS) == 4) m = (unsigned long long)__double_as_longlong((double)__uint_as_float((unsigned)m));
+        for (int i = 1; i < NRED; ++i) mx = red[i][col] > mx ? red[i][col] : mx;
+        if (mx != 0) {
+            if constexpr (sizeof(TS) == 4) mx = (unsigned long long)__double_as_longlong((double)__uint_as_float((unsigned)mx));
             unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
-            atomicMax(ex + tk.c0 + col, m);
+            atomicMax(ex + tk.c0 + col, mx);
         }
     }
 }
 
-// Balanced base-256 digits of round(x * 2^(8S - E)), most significant first:
-// x * 2^-E ~= sum_s d[s] * 2^(-8(s+1)), |d[0]| <= 256 >> HEAD (E carries the
-// column's headroom), |d[s>0]| <= 128.
-// Integer arithmetic only (the FP64 pipe is not involved).
+// Balanced base-256 digits of v = round(x * 2^(8S - E)), most significant
+// first: x * 2^-E ~= sum_s d[s] * 2^(-8(s+1)), |d[0]| <= 256 >> HEAD (E
+// carries the column's headroom), d[s>0] in [-128, 127].  They are returned
+// biased, b[s] = d[s] + 128: adding 128 to every base-256 position below the
+// top one turns the balanced digits into the plain bytes of u = v + bias
+// (each d[s] + 128 lies in [0, 255]), and the top digit is the arithmetic
+// shift of u.  Integer arithmetic only.
 template <int S>
-__device__ __forceinline__ void slice_digits(double x, int E, int (&d)[S]) {
+__device__ __forceinline__ void biased_digits(double x, int E, int (&b)[S]) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
     long long v = 0;
@@ -589,17 +604,15 @@ __device__ __forceinline__ void slice_digits(double x, int E, int (&d)[S]) {
             v = (m + (1LL << (-shift - 1))) >> (-shift);
         if (bits < 0) v = -v;
     }
+    constexpr long long bias = (long long)(((unsigned long long)1 << (8 * (S - 1))) - 1) / 255 * 128;
+    const long long u = v + bias;
 #pragma unroll
-    for (int s = S - 1; s >= 1; --s) {
-        const long long r = ((v + 128) & 255) - 128;
-        d[s] = (int)r;
-        v = (v - r) >> 8;
-    }
-    d[0] = (int)v;
+    for (int s = 1; s < S; ++s) b[s] = (int)((u >> (8 * (S - 1 - s))) & 255);
+    b[0] = (int)(u >> (8 * (S - 1))) + 128;
 }
 
 // The same for an FP32 value and S = 3 (24 bits) in 32-bit integers.
-__device__ __forceinline__ void slice_digits(float x, int E, int (&d)[3]) {
+__device__ __forceinline__ void biased_digits(float x, int E, int (&b)[3]) {
     const unsigned int bits = __float_as_uint(x);
     const int eb = (int)((bits >> 23) & 0xFF);
     int v = 0;
@@ -612,13 +625,34 @@ __device__ __forceinline__ void slice_digits(float x, int E, int (&d)[3]) {
             v = (int)(((long long)m + (1LL << (-shift - 1))) >> (-shift));
         if (bits >> 31) v = -v;
     }
-#pragma unroll
-    for (int s = 2; s >= 1; --s) {
-        const int r = ((v + 128) & 255) - 128;
-        d[s] = r;
-        v = (v - r) >> 8;
-    }
-    d[0] = v;
+    const int u = v + 0x8080;
+    b[2] = u & 255;
+    b[1] = (u >> 8) & 255;
+    b[0] = (u >> 16) + 128;
+}
+
+// bf16 bit pattern of (b - 128) * 2^-8(s+1) for a biased digit b in
+// [-128, 384]: b is placed in the significand of 1.5 * 2^23 (exact integer
+// float), one FMA removes the offset and applies the power of two (exact: the
+// result has at most 9 significant bits), and the bf16 is the upper half of
+// the float's bits, exact since its low 16 bits are zero.
+__host__ __device__ constexpr float exp2_neg(int e) {
+    float r = 1.0f;
+    for (int i = 0; i < e; ++i) r *= 0.5f;
+    return r;
+}
+
+template <int s>
+__device__ __forceinline__ uint32_t digit_f32_bits(int b) {
+    constexpr float scale = exp2_neg(8 * (s + 1));
+    const float f = __int_as_float(0x4B400000 + b);  // 12582912 + b
+    return __float_as_uint(fmaf(f, scale, -12583040.0f * scale));  // (12582912 + 128) * scale
+}
+
+// Two bf16 (the upper halves of lo's and hi's float bits) in one 32-bit word,
+// lo at the lower address.
+__device__ __forceinline__ uint32_t pack_bf16_hi(uint32_t lo_bits, uint32_t hi_bits) {
+    return __byte_perm(lo_bits, hi_bits, 0x7632);
 }
 
 template <int MODE>
@@ -629,6 +663,20 @@ template <>
 struct PrepSrc<MODE_OZAKI> {
     using T = double;
 };
+
+// Writes the S parts of 8 consecutive K values of one column: part s gets
+// the 8 bf16 of digit s, 16 bytes at out + s * part_elems + base.
+template <int S, int s = 0>
+__device__ __forceinline__ void store_parts(const int (&dg)[8][S], __nv_bfloat16* out, int64_t part_elems,
+                                            int64_t base) {
+    uint4 q;
+    q.x = pack_bf16_hi(digit_f32_bits<s>(dg[0][s]), digit_f32_bits<s>(dg[1][s]));
+    q.y = pack_bf16_hi(digit_f32_bits<s>(dg[2][s]), digit_f32_bits<s>(dg[3][s]));
+    q.z = pack_bf16_hi(digit_f32_bits<s>(dg[4][s]), digit_f32_bits<s>(dg[5][s]));
+    q.w = pack_bf16_hi(digit_f32_bits<s>(dg[6][s]), digit_f32_bits<s>(dg[7][s]));
+    *reinterpret_cast<uint4*>(out + s * part_elems + base) = q;
+    if constexpr (s + 1 < S) store_parts<S, s + 1>(dg, out, part_elems, base);
+}
 
 // Parts of one 64 (K) x 64 (column) tile of a leaf operand, written K-major:
 // part q of column c, K index k at parts + ((q * rows_pad + c) * K_pad + k).
@@ -675,16 +723,9 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
             const int E = col_exponent<Geo<MODE>::HEAD>(mx);
             int dg[8][S];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) slice_digits(tile[kc * 8 + i][col], E, dg[i]);
+            for (int i = 0; i < 8; ++i) biased_digits(tile[kc * 8 + i][col], E, dg[i]);
             __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const float unit = __int_as_float((127 - 8 * (s + 1)) << 23);  // 2^-8(s+1)
-                __nv_bfloat16 q[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) q[i] = __float2bfloat16_rn(__int2float_rn(dg[i][s]) * unit);
-                *reinterpret_cast<uint4*>(out + s * part_elems + base) = *reinterpret_cast<const uint4*>(q);
-            }
+            store_parts<S>(dg, out, part_elems, base);
         }
     }
 }
@@ -1132,8 +1173,9 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
     if (Geo<MODE>::SLICED) {
         cudaError_t e = cudaMemsetAsync(t.tc_ex, 0, t.tc_ex_bytes, s);
         if (e != cudaSuccess) return e;
-        if (t.nprep > 0)
-            tc_colmax_kernel<NB, typename PrepSrc<MODE>::T><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
+        if (t.ncolmax > 0)
+            tc_colmax_kernel<NB, typename PrepSrc<MODE>::T>
+                <<<t.ncolmax, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.colmax);
     }
     if (t.nprep > 0) tc_prep_kernel<NB, MODE><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
     if (before_gemm) {
@@ -1246,7 +1288,7 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     if (st != ATA_OK) return st;
     const int np = (int)h.prods.size();
     std::vector<TcProd> tp(np);
-    std::vector<PrepTask> prep;
+    std::vector<PrepTask> prep, colmax;
     int64_t ex_elems = 0;
     for (int i = 0; i < np; ++i) {
         const LeafProduct& lp = h.prods[i];
@@ -1276,22 +1318,35 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         if (!syrk) ex_elems += lp.r_pad;
         for (int side = 0; side < (syrk ? 1 : 2); ++side) {
             const int rows_pad = side ? lp.r_pad : lp.p_pad;
-            for (int c0 = 0; c0 < rows_pad; c0 += PT)
+            for (int c0 = 0; c0 < rows_pad; c0 += PT) {
                 for (int k0 = 0; k0 < lp.K_pad; k0 += PT) {
-                    PrepTask pt;
+                    PrepTask pt{};
                     pt.prod = i;
                     pt.side = (int8_t)side;
                     pt.c0 = c0;
                     pt.k0 = k0;
+                    pt.k1 = k0 + PT;
                     prep.push_back(pt);
                 }
+                // column maxima over the valid rows only
+                for (int k0 = 0; k0 < lp.K; k0 += kColSpan) {
+                    PrepTask ct{};
+                    ct.prod = i;
+                    ct.side = (int8_t)side;
+                    ct.c0 = c0;
+                    ct.k0 = k0;
+                    ct.k1 = std::min(k0 + kColSpan, lp.K);
+                    colmax.push_back(ct);
+                }
+            }
         }
     }
-    // device blob: TcProd[] | PrepTask[] | status | exponent maxima
+    // device blob: TcProd[] | PrepTask[] (slicing) | PrepTask[] (maxima) | status | exponent maxima
     auto al = [](int64_t x) { return (x + 255) / 256 * 256; };
     const int64_t o_tp = 0;
     const int64_t o_prep = al(o_tp + (int64_t)np * sizeof(TcProd));
-    const int64_t o_status = al(o_prep + (int64_t)prep.size() * sizeof(PrepTask));
+    const int64_t o_colmax = al(o_prep + (int64_t)prep.size() * sizeof(PrepTask));
+    const int64_t o_status = al(o_colmax + (int64_t)colmax.size() * sizeof(PrepTask));
     const int64_t o_ex = al(o_status + 256);
     const int64_t total = al(o_ex + std::max<int64_t>(ex_elems, 1) * 8);
     char* blob = nullptr;
@@ -1306,6 +1361,7 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     std::vector<char> hb(total, 0);
     if (np) std::memcpy(hb.data() + o_tp, tp.data(), np * sizeof(TcProd));
     if (!prep.empty()) std::memcpy(hb.data() + o_prep, prep.data(), prep.size() * sizeof(PrepTask));
+    if (!colmax.empty()) std::memcpy(hb.data() + o_colmax, colmax.data(), colmax.size() * sizeof(PrepTask));
     cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
@@ -1315,6 +1371,8 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     d->tcp = reinterpret_cast<TcProd*>(blob + o_tp);
     d->prep = reinterpret_cast<PrepTask*>(blob + o_prep);
     d->nprep = (int)prep.size();
+    d->colmax = reinterpret_cast<PrepTask*>(blob + o_colmax);
+    d->ncolmax = (int)colmax.size();
     d->status = reinterpret_cast<int*>(blob + o_status);
     d->tc_ex = blob + o_ex;
     d->tc_ex_bytes = (size_t)std::max<int64_t>(ex_elems, 1) * 8;

@@ -33,12 +33,15 @@ struct alignas(64) TcProd {
     int64_t ex_index, ey_index;
 };
 
-// One 64 (K) x 32 (column) tile of a leaf operand for the preparation kernels.
+// A 64-column strip of a leaf operand for the preparation kernels: rows
+// [k0, k1) of columns [c0, c0 + 64) (one 64 x 64 tile for the slicing
+// kernel, up to kColSpan rows for the column-maximum kernel).
 struct PrepTask {
     int32_t prod;
     int8_t side, pad_[3];
-    int32_t c0, k0;
+    int32_t c0, k0, k1;
 };
+constexpr int kColSpan = 1024;
 
 // Task tables on the host, ready to upload (one plan or a merged batch).
 struct HostTables {
@@ -78,6 +81,8 @@ struct DeviceTables {
     TcProd* tcp = nullptr;
     PrepTask* prep = nullptr;
     int nprep = 0;
+    PrepTask* colmax = nullptr;  // column-maximum strips (sliced modes)
+    int ncolmax = 0;
     int* status = nullptr;     // device error word of the tensor-core kernels
     char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
     size_t tc_ex_bytes = 0;

@@ -273,6 +273,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without the wait: several loads may be in flight; the
+// registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -333,6 +351,35 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
     two_sum(hi, x, s, e);
     hi = s;
     lo += e;
+}
+
+// Two FP32 lanes in one 64-bit register: the packed f32x2 instructions add
+// or subtract both lanes with IEEE round-to-nearest, so every lane computes
+// exactly what the scalar instruction would, at half the instruction count.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float x, float y) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& x, float& y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// TwoSum on both lanes.
+__device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2& s, f32x2& e) {
+    s = add2(a, b);
+    const f32x2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
 __device__ __forceinline__ int64_t packed_start(int64_t i, int64_t n) { return i * n - i * (i - 1) / 2; }
@@ -755,7 +802,10 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
     constexpr int NKS = G::KBLK / G::KSTEP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* lo_s = reinterpret_cast<float*>(smem + NSTAGE * SH::STAGE);  // [col][row]
+    // lo halves of the running float-float sums, column pairs interleaved:
+    // element (row, col) at lo_s[((col / 2) * 128 + row) * 2 + col % 2]
+    float* lo_s = reinterpret_cast<float*>(smem + NSTAGE * SH::STAGE);
+    f32x2* lo2_s = reinterpret_cast<f32x2*>(lo_s);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * SH::STAGE + SH::LO);
     // barriers: full[NSTAGE] empty[NSTAGE] dfull[DBUF] dempty[DBUF] ffull fempty done ; tmem slot
     const uint32_t b_full = smem_u32(bars), b_empty = b_full + 8 * NSTAGE;
@@ -965,30 +1015,34 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
                         const uint32_t col = cq * NCOL + g * 16;
-                        float a0[16], a1[16];
-                        tmem_ld16(tmem + lane_base + (buf * G::ND + 0) * 128 + col, a0);
-                        tmem_ld16(tmem + lane_base + (buf * G::ND + 1) * 128 + col, a1);
-                        float a2[16];
-                        if constexpr (G::ND > 2) {
-                            tmem_ld16(tmem + lane_base + (buf * G::ND + 2) * 128 + col, a2);
-                        } else {
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) a2[c] = 0.f;
-                        }
+                        for (int c8 = 0; c8 < 16; c8 += 8) {
+                        // the accumulators' 8 columns in flight together, one wait
+                        uint32_t a0[8], a1[8], a2[8];
+                        tmem_ld8_async(tmem + lane_base + (buf * G::ND + 0) * 128 + col + c8, a0);
+                        tmem_ld8_async(tmem + lane_base + (buf * G::ND + 1) * 128 + col + c8, a1);
+                        if constexpr (G::ND > 2)
+                            tmem_ld8_async(tmem + lane_base + (buf * G::ND + 2) * 128 + col + c8, a2);
+                        tmem_wait_ld();
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) {
+                        for (int cc = 0; cc < 8; cc += 2) {
+                            const int c = c8 + cc;
                             // chunk value h + l (accumulator 0 is exact, the others are at
                             // most ~2^-8 of it), added to (hi, lo) as a float-float sum and
-                            // renormalised so that |lo| stays within half an ulp of hi
-                            float h, l, s2, e2;
-                            two_sum(a0[c], a1[c], h, l);
-                            l += a2[c];
-                            float* lp = lo_s + (col + c) * 128 + row;
-                            two_sum(hi[g * 16 + c], h, s2, e2);
-                            e2 += (ci == 0 ? 0.f : *lp) + l;
-                            const float hn = s2 + e2;       // Fast2Sum: |s2| >= |e2|
-                            *lp = e2 - (hn - s2);
-                            hi[g * 16 + c] = hn;
+                            // renormalised so that |lo| stays within half an ulp of hi;
+                            // two columns per instruction
+                            f32x2 h, l, s2, e2;
+                            two_sum2(pk2(__uint_as_float(a0[cc]), __uint_as_float(a0[cc + 1])),
+                                     pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1])), h, l);
+                            if constexpr (G::ND > 2)
+                                l = add2(l, pk2(__uint_as_float(a2[cc]), __uint_as_float(a2[cc + 1])));
+                            f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
+                            two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]), h, s2, e2);
+                            e2 = add2(e2, add2(ci == 0 ? 0ull : *lp, l));
+                            const f32x2 hn = add2(s2, e2);  // Fast2Sum: |s2| >= |e2|
+                            *lp = sub2(e2, sub2(hn, s2));
+                            upk2(hn, hi[g * 16 + c], hi[g * 16 + c + 1]);
+                        }
                         }
                     }
                     tc_fence_before();
@@ -1011,7 +1065,10 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                             float f[16];
                             tmem_ld16(tmem + lane_base + G::F_COL + col, f);
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) lo_s[(col + c) * 128 + row] += f[c];
+                            for (int c = 0; c < 16; c += 2) {
+                                f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
+                                *lp = add2(*lp, pk2(f[c], f[c + 1]));
+                            }
                         }
                         tc_fence_before();
                         __syncwarp();
@@ -1060,7 +1117,8 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                     for (int c = 0; c < 16; ++c) {
                         const int j = j0 + g * 16 + c;
                         if (j < pr->out_cols) {
-                            float hh = hi[g * 16 + c], ll = G::ND > 0 ? lo_s[(col + c) * 128 + row] : 0.f;
+                            float hh = hi[g * 16 + c],
+                                  ll = G::ND > 0 ? lo_s[(((col + c) / 2) * 128 + row) * 2 + ((col + c) & 1)] : 0.f;
                             ff_add(hh, ll, f[c]);
                             long long bh = f2d_bits(hh), bl = f2d_bits(ll);
                             double v;

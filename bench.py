@@ -96,9 +96,15 @@ def tensor_peak(mode):
         return bf16 * 1.1 / 2.25, f"{src} bf16 x nominal tf32/bf16"
     return bf16, f"{src} bf16 (burst)"
 
-# DRAM traffic of the leaf kernel from one ncu capture, per launch, valid only
-# for the kernel source it was taken on (sha256 of kernels_f64.cu).
-LEAF_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the leaf kernel on the full-size workload, from a one-pass ncu capture
+# (profiles/), valid only for the kernel source it was taken on (the first 16
+# hex digits of the sha256 of leaf_tc.cu or kernels_f64.cu).
+LEAF_TRAFFIC = {
+    ("ata_ozaki_10000x10000", "a8d186eaf307bf2f"): 15.370e9 + 0.559e9,
+    ("ata_bf16x3_16384x8192", "a8d186eaf307bf2f"): 6.085e9 + 0.287e9,
+    ("ata_f64_10000x10000", "beaf79f07d6f1ff4"): 35.899e9 + 4.653e9,
+}
 
 
 def _src_sha(path):

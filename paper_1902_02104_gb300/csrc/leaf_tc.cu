@@ -305,12 +305,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 
 // Exact FP32 -> FP64 widening with integer operations (the FP64 pipe is the
 // scarce unit on this part); zero and subnormal inputs give 0, which changes
-// a result by less than 2^-126 of its unit.
+// a result by less than 2^-126 of its unit; Inf and NaN stay Inf and NaN.
 __device__ __forceinline__ long long f2d_bits(float f) {
     const unsigned int b = __float_as_uint(f);
     const unsigned int e = (b >> 23) & 0xFF;
     if (e == 0) return 0;
-    return ((long long)(b >> 31) << 63) | ((long long)(e + 896) << 52) | ((long long)(b & 0x7FFFFF) << 29);
+    const long long eb = e == 0xFF ? 0x7FF : (long long)(e + 896);
+    return ((long long)(b >> 31) << 63) | (eb << 52) | ((long long)(b & 0x7FFFFF) << 29);
 }
 
 // Scale exponent E of a column whose largest magnitude has bit pattern mx:

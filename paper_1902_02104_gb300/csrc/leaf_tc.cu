@@ -394,7 +394,9 @@ __device__ __forceinline__ int64_t packed_start(int64_t i, int64_t n) { return i
 //   F group: the other orders (FMIN..FMAX) in one accumulator, either over
 //            the whole K (F_FINAL) or drained per chunk like the D group.
 // The float-float running sums (hi, lo) of a thread's columns: hi in
-// registers, lo in shared memory.
+// registers, lo in shared memory.  FP64_SUM: the output is hi + lo in FP64
+// (the FP64 emulation); otherwise the FP32 sum of the pair, widened exactly
+// (the FP32-accuracy modes, whose results carry 24 bits).
 
 template <int MODE>
 struct Geo;
@@ -415,7 +417,7 @@ struct Geo<MODE_BF16X3> {
     static constexpr int PARTS = 3, ELEM = 2, KBLK = 32, ROWB = 64, KSTEP = 16, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 4, SBO = 512;  // 64B swizzle
     static constexpr int KC = 256, ND = 2, DMAX = 2, DBUF = 2, FMIN = 1, FMAX = 0, HEAD = 0;  // no F group
-    static constexpr bool F_FINAL = false, SLICED = true;
+    static constexpr bool F_FINAL = false, SLICED = true, FP64_SUM = false;
     static constexpr int EPI_WARPS = 16;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 0;
     static constexpr uint32_t IDESC_KIND = (1u << 4) | (1u << 7) | (1u << 10);  // F32 D, bf16 A and B
@@ -426,7 +428,7 @@ struct Geo<MODE_TF32> {
     static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6, NSTAGE2 = 8;
     static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
     static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0, HEAD = 0;
-    static constexpr bool F_FINAL = true, SLICED = false;
+    static constexpr bool F_FINAL = true, SLICED = false, FP64_SUM = false;
     static constexpr int EPI_WARPS = 8;
     static constexpr uint32_t TMEM_COLS = 128, F_COL = 0;
     static constexpr uint32_t IDESC_KIND = (1u << 4) | (2u << 7) | (2u << 10);  // F32 D, tf32 A and B
@@ -437,7 +439,7 @@ struct Geo<MODE_OZAKI> {
     static constexpr int PARTS = 6, ELEM = 2, KBLK = 16, ROWB = 32, KSTEP = 16, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 6, SBO = 256;  // 32B swizzle
     static constexpr int KC = 256, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5, HEAD = 0;
-    static constexpr bool F_FINAL = false, SLICED = true;
+    static constexpr bool F_FINAL = false, SLICED = true, FP64_SUM = true;
     static constexpr int EPI_WARPS = 16;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 384;
     static constexpr uint32_t IDESC_KIND = (1u << 4) | (1u << 7) | (1u << 10);  // F32 D, bf16 A and B
@@ -1090,19 +1092,24 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                 }
                 tc_fence_after();
             }
-            // FP64 tile: row i of this thread, NCOL columns in groups of 16
+            // FP64 tile: row i of this thread, NCOL columns in groups of 16.  The
+            // product's fields are read once into registers: the output stores
+            // below could alias the table as far as the compiler knows.
+            const int p_out_rows = __ldg(&pr->out_rows), p_out_cols = __ldg(&pr->out_cols);
+            const int p_out_kind = __ldg(&pr->out_kind), p_cj0 = __ldg(&pr->cj0);
+            const unsigned long long* __restrict__ p_ey = reinterpret_cast<const unsigned long long*>(pr->ey);
             const Bind& bind = bs.b[pr->inst];
             const int i = lt.ti * (128 * CG) + (int)rank * 128 + row;
             const int j0 = lt.tj * 128 + cq * NCOL;
-            const bool row_ok = i < pr->out_rows;
+            const bool row_ok = i < p_out_rows;
             int Ei = 0;
             if constexpr (G::SLICED) {
-                if (row_ok) Ei = col_exponent<G::HEAD>(reinterpret_cast<const unsigned long long*>(pr->ex)[i]);
+                if (row_ok) Ei = col_exponent<G::HEAD>(__ldg(reinterpret_cast<const unsigned long long*>(pr->ex) + i));
             }
-            double* dense = (pr->out_kind == OUT_CDENSE ? bind.C : reinterpret_cast<double*>(bind.W)) + pr->out_off +
+            double* dense = (p_out_kind == OUT_CDENSE ? bind.C : reinterpret_cast<double*>(bind.W)) + pr->out_off +
                             (int64_t)i * pr->out_ld;
             const int64_t gi = (int64_t)pr->ci0 + i;
-            double* prow = bind.C + (packed_start(gi, bind.n) - gi + pr->cj0);
+            double* prow = bind.C + (packed_start(gi, bind.n) - gi + p_cj0);
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const uint32_t col = cq * NCOL + g * 16;
@@ -1114,29 +1121,54 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                     for (int c = 0; c < 16; ++c) f[c] = 0.f;
                 }
                 if (row_ok) {
+                    const bool dense_out = p_out_kind == OUT_DENSE || p_out_kind == OUT_CDENSE;
+                    double* dst = (dense_out ? dense : prow) + j0 + g * 16;
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const int j = j0 + g * 16 + c;
-                        if (j < pr->out_cols) {
+                    for (int c4 = 0; c4 < 16; c4 += 4) {
+                        double v[4];
+                        bool ok[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = c4 + q;
+                            const int j = j0 + g * 16 + c;
+                            ok[q] = j < p_out_cols && (dense_out || p_out_kind == OUT_PACKED || (int64_t)p_cj0 + j >= gi);
                             float hh = hi[g * 16 + c],
                                   ll = G::ND > 0 ? lo_s[(((col + c) / 2) * 128 + row) * 2 + ((col + c) & 1)] : 0.f;
                             ff_add(hh, ll, f[c]);
+                            if constexpr (!G::FP64_SUM) {
+                                // FP32-accuracy modes: the FP32 sum of the pair, widened
+                                // with integer operations (no FP64 arithmetic per entry)
+                                hh += ll;
+                                ll = 0.f;
+                            }
                             long long bh = f2d_bits(hh), bl = f2d_bits(ll);
-                            double v;
+                            int sc = 0;
                             if constexpr (G::SLICED) {
-                                const int sc = Ei + col_exponent<G::HEAD>(reinterpret_cast<const unsigned long long*>(pr->ey)[j]);
+                                sc = Ei + col_exponent<G::HEAD>(__ldg(p_ey + j));
                                 if (bh) bh += (long long)sc << 52;
                                 if (bl) bl += (long long)sc << 52;
-                                v = sc >= kNonFinite ? __longlong_as_double(0x7FF8000000000000LL)
-                                                     : __longlong_as_double(bh) + __longlong_as_double(bl);
-                            } else {
-                                v = __longlong_as_double(bh) + __longlong_as_double(bl);
                             }
-                            if (pr->out_kind == OUT_DENSE || pr->out_kind == OUT_CDENSE) {
-                                dense[j] = v;
-                            } else if (pr->out_kind == OUT_PACKED || (int64_t)pr->cj0 + j >= gi) {
-                                prow[j] = v;
-                            }
+                            if (G::SLICED && sc >= kNonFinite)
+                                v[q] = __longlong_as_double(0x7FF8000000000000LL);
+                            else if constexpr (G::FP64_SUM)
+                                v[q] = __longlong_as_double(bh) + __longlong_as_double(bl);
+                            else
+                                v[q] = __longlong_as_double(bh);
+                        }
+                        // whole 32-byte sectors where the row segment allows it
+                        double* d = dst + c4;
+                        const uintptr_t a = reinterpret_cast<uintptr_t>(d);
+                        if (ok[0] && ok[1] && ok[2] && ok[3] && (a & 31) == 0) {
+                            asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(d), "d"(v[0]), "d"(v[1]),
+                                         "d"(v[2]), "d"(v[3])
+                                         : "memory");
+                        } else if (ok[0] && ok[1] && ok[2] && ok[3] && (a & 15) == 0) {
+                            *reinterpret_cast<double2*>(d) = make_double2(v[0], v[1]);
+                            *reinterpret_cast<double2*>(d + 2) = make_double2(v[2], v[3]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (ok[q]) d[q] = v[q];
                         }
                     }
                 }
@@ -1376,8 +1408,11 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         t.ey_index = syrk ? t.ex_index : ex_elems;
         if (!syrk) ex_elems += lp.r_pad;
         for (int side = 0; side < (syrk ? 1 : 2); ++side) {
-            const int rows_pad = side ? lp.r_pad : lp.p_pad;
-            for (int c0 = 0; c0 < rows_pad; c0 += PT) {
+            // Part rows past the product's output extent feed only output rows
+            // or columns that are never written, so whole 64-row blocks of them
+            // are not prepared (their contents are never read into a result).
+            const int rows_used = side ? lp.out_cols : lp.out_rows;
+            for (int c0 = 0; c0 < rows_used; c0 += PT) {
                 for (int k0 = 0; k0 < lp.K_pad; k0 += PT) {
                     PrepTask pt{};
                     pt.prod = i;

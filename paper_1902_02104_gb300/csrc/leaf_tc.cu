@@ -40,6 +40,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -1381,6 +1382,16 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     std::vector<TcProd> tp(np);
     std::vector<PrepTask> prep, colmax;
     int64_t ex_elems = 0;
+    // Operands that share a part buffer (equal terms, see the planner) are
+    // prepared once, by their first product, over the rows any user needs,
+    // and share one column-maximum array.
+    struct Buf {
+        int prod, side;
+        int rows_used;
+        int64_t ex_index;
+    };
+    std::map<std::pair<int, int64_t>, Buf> bufs;
+    std::vector<std::pair<int, int64_t>> order;  // first-use order
     for (int i = 0; i < np; ++i) {
         const LeafProduct& lp = h.prods[i];
         TcProd& t = tp[i];
@@ -1402,36 +1413,48 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         t.out_off = lp.out_off;
         t.ci0 = lp.ci0;
         t.cj0 = lp.cj0;
-        t.ex_index = ex_elems;
-        ex_elems += lp.p_pad;
         const bool syrk = lp.out_kind == OUT_SYRK;
-        t.ey_index = syrk ? t.ex_index : ex_elems;
-        if (!syrk) ex_elems += lp.r_pad;
         for (int side = 0; side < (syrk ? 1 : 2); ++side) {
             // Part rows past the product's output extent feed only output rows
             // or columns that are never written, so whole 64-row blocks of them
             // are not prepared (their contents are never read into a result).
             const int rows_used = side ? lp.out_cols : lp.out_rows;
-            for (int c0 = 0; c0 < rows_used; c0 += PT) {
-                for (int k0 = 0; k0 < lp.K_pad; k0 += PT) {
-                    PrepTask pt{};
-                    pt.prod = i;
-                    pt.side = (int8_t)side;
-                    pt.c0 = c0;
-                    pt.k0 = k0;
-                    pt.k1 = k0 + PT;
-                    prep.push_back(pt);
-                }
-                // column maxima over the valid rows only
-                for (int k0 = 0; k0 < lp.K; k0 += kColSpan) {
-                    PrepTask ct{};
-                    ct.prod = i;
-                    ct.side = (int8_t)side;
-                    ct.c0 = c0;
-                    ct.k0 = k0;
-                    ct.k1 = std::min(k0 + kColSpan, lp.K);
-                    colmax.push_back(ct);
-                }
+            const auto key = std::make_pair(lp.inst, side ? lp.tc_y_off : lp.tc_x_off);
+            auto it = bufs.find(key);
+            if (it == bufs.end()) {
+                Buf b{i, side, rows_used, ex_elems};
+                ex_elems += side ? lp.r_pad : lp.p_pad;
+                it = bufs.emplace(key, b).first;
+                order.push_back(key);
+            } else {
+                it->second.rows_used = std::max(it->second.rows_used, rows_used);
+            }
+            if (side == 0) t.ex_index = it->second.ex_index;
+            if (side == 1 || syrk) t.ey_index = it->second.ex_index;
+        }
+    }
+    for (const auto& key : order) {
+        const Buf& b = bufs[key];
+        const LeafProduct& lp = h.prods[b.prod];
+        for (int c0 = 0; c0 < b.rows_used; c0 += PT) {
+            for (int k0 = 0; k0 < lp.K_pad; k0 += PT) {
+                PrepTask pt{};
+                pt.prod = b.prod;
+                pt.side = (int8_t)b.side;
+                pt.c0 = c0;
+                pt.k0 = k0;
+                pt.k1 = k0 + PT;
+                prep.push_back(pt);
+            }
+            // column maxima over the valid rows only
+            for (int k0 = 0; k0 < lp.K; k0 += kColSpan) {
+                PrepTask ct{};
+                ct.prod = b.prod;
+                ct.side = (int8_t)b.side;
+                ct.c0 = c0;
+                ct.k0 = k0;
+                ct.k1 = std::min(k0 + kColSpan, lp.K);
+                colmax.push_back(ct);
             }
         }
     }

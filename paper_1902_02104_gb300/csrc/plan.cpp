@@ -2,6 +2,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <map>
 #include <cstring>
 
 namespace ata {
@@ -78,9 +79,27 @@ struct Ctx {
     Plan* P;
     const PlanOptions* opt;
     int64_t ws = 0;
+    // tensor-core part buffers by operand: equal operands (the same signed
+    // terms, K and padding) share one buffer, prepared once
+    std::map<std::vector<int64_t>, int64_t> parts;
     int64_t alloc(int64_t bytes) {
         int64_t off = ws;
         ws += (bytes + kAlign - 1) / kAlign * kAlign;
+        return off;
+    }
+    int64_t parts_buffer(const std::vector<Term>& ts, int64_t K, int32_t rows_pad, int32_t K_pad, int8_t dt,
+                         int64_t bytes) {
+        std::vector<int64_t> key{K, rows_pad, K_pad, dt};
+        for (const Term& t : ts) {
+            key.push_back(t.off);
+            key.push_back(t.ld);
+            key.push_back(((int64_t)t.rows << 32) | (uint32_t)t.cols);
+            key.push_back(t.buf * 16 + t.dt * 4 + t.neg);
+        }
+        auto it = parts.find(key);
+        if (it != parts.end()) return it->second;
+        const int64_t off = alloc(bytes);
+        parts.emplace(std::move(key), off);
         return off;
     }
 };
@@ -148,8 +167,10 @@ void emit_leaf(Ctx& c, const std::vector<Term>& X, const std::vector<Term>& Y, i
         lp.p_pad = (int32_t)((p + xr - 1) / xr * xr);
         lp.r_pad = syrk ? lp.p_pad : (int32_t)((r + kTcTile - 1) / kTcTile * kTcTile);
         lp.K_pad = (int32_t)std::max<int64_t>((K + g.k_align - 1) / g.k_align * g.k_align, g.k_align);
-        lp.tc_x_off = c.alloc((int64_t)g.parts * lp.p_pad * lp.K_pad * g.elem);
-        lp.tc_y_off = syrk ? lp.tc_x_off : c.alloc((int64_t)g.parts * lp.r_pad * lp.K_pad * g.elem);
+        lp.tc_x_off = c.parts_buffer(X, K, lp.p_pad, lp.K_pad, x_dt, (int64_t)g.parts * lp.p_pad * lp.K_pad * g.elem);
+        lp.tc_y_off = syrk ? lp.tc_x_off
+                           : c.parts_buffer(Y, K, lp.r_pad, lp.K_pad, y_dt,
+                                            (int64_t)g.parts * lp.r_pad * lp.K_pad * g.elem);
     }
     if (syrk) {
         lp.out_kind = OUT_SYRK;

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 
 #include "runtime.h"
@@ -42,16 +43,19 @@ Rates rates_for(ata_dtype d) {
     return {0.6e12, 0.5e12, 6e12};
 }
 
-// Bytes the operand preparation of the tensor-core leaves moves: every leaf
-// operand element is read twice (column maxima, slicing) and written as its
-// parts.
+// Bytes the operand preparation of the tensor-core leaves moves: every
+// distinct leaf operand (operands with equal terms share one part buffer)
+// element is read twice (column maxima, slicing) and written as its parts.
 double prep_bytes(const Plan& P) {
     if (P.leaf == LEAF_F64) return 0.0;
     const TcGeom g = tc_geom(P.leaf);
     const double in = P.in_dt == DT_F64 ? 8.0 : 4.0;
     double elems = 0;
-    for (const LeafProduct& lp : P.products)
-        elems += (double)lp.K_pad * (lp.p_pad + (lp.out_kind == OUT_SYRK ? 0 : lp.r_pad));
+    std::set<int64_t> seen;
+    for (const LeafProduct& lp : P.products) {
+        if (seen.insert(lp.tc_x_off).second) elems += (double)lp.K_pad * lp.p_pad;
+        if (lp.out_kind != OUT_SYRK && seen.insert(lp.tc_y_off).second) elems += (double)lp.K_pad * lp.r_pad;
+    }
     return elems * (2.0 * in + g.parts * g.elem);
 }
 

@@ -222,10 +222,12 @@ def dist_setup():
 
 
 def max_over_ranks(torch, value, world):
+    """The largest of every rank's value (the slowest replica sets the time)."""
     if world == 1:
         return value
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

@@ -145,7 +145,9 @@ typedef struct {
     int32_t fuse_levels;         /* bottom Strassen levels whose operand sums
                                     are formed inside the leaf loads instead of
                                     materialised (-1 = dtype default: 0 for
-                                    the FP64 modes, 1 for the FP32 modes)      */
+                                    ATA_F64; for ATA_F64_OZAKI 1 (sums formed
+                                    in fixed point while slicing), 0 with
+                                    Winograd's variant; 1 for the FP32 modes) */
     int32_t max_strassen_levels; /* cap on Strassen levels per product
                                     (-1 = none; 0 = classical products)        */
     int32_t cta_pair;            /* tensor-core leaves: 1 = 256 x 128 output

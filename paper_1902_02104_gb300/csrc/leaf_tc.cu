@@ -44,6 +44,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "runtime.h"
@@ -641,8 +642,10 @@ __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ 
 // top one turns the balanced digits into the plain bytes of u = v + bias
 // (each d[s] + 128 lies in [0, 255]), and the top digit is the arithmetic
 // shift of u.  Integer arithmetic only.
+// v = round(x * 2^(8S - E)) from the bits of x (integer arithmetic only); 0
+// for zero, subnormal and non-finite x or a non-finite column.
 template <int S>
-__device__ __forceinline__ void biased_digits(double x, int E, int (&b)[S]) {
+__device__ __forceinline__ long long fixed_point(double x, int E) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
     long long v = 0;
@@ -655,11 +658,22 @@ __device__ __forceinline__ void biased_digits(double x, int E, int (&b)[S]) {
             v = (m + (1LL << (-shift - 1))) >> (-shift);
         if (bits < 0) v = -v;
     }
+    return v;
+}
+
+// Biased digits of a fixed-point value v (|v| <= 2^(8S) + a few units).
+template <int S>
+__device__ __forceinline__ void digits_of(long long v, int (&b)[S]) {
     constexpr long long bias = (long long)(((unsigned long long)1 << (8 * (S - 1))) - 1) / 255 * 128;
     const long long u = v + bias;
 #pragma unroll
     for (int s = 1; s < S; ++s) b[s] = (int)((u >> (8 * (S - 1 - s))) & 255);
     b[0] = (int)(u >> (8 * (S - 1))) + 128;
+}
+
+template <int S>
+__device__ __forceinline__ void biased_digits(double x, int E, int (&b)[S]) {
+    digits_of<S>(fixed_point<S>(x, E), b);
 }
 
 // The same for an FP32 value and S = 3 (24 bits) in 32-bit integers.
@@ -778,6 +792,147 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
             __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
             store_parts<S>(dg, out, part_elems, base);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 emulation: operands formed in fixed point
+//
+// A leaf operand is a signed sum of blocks (of A, or of materialised sums).
+// Its column c is scaled by 2^-E(c) with
+//     E(c) = max_t E_t(c) + ceil(log2 n(c)),
+// E_t(c) the exponent of block t's column maximum and n(c) the number of
+// blocks with a nonzero column c, so that |sum| <= n(c) max_t |x_t| < 2^E(c).
+// Every block value is converted exactly to the fixed point of that scale
+// (rounded to the nearest unit of 2^(E - 48)) and the blocks are added in
+// 64-bit integers: the Strassen operand sums are formed without
+// floating-point arithmetic, each term adding at most half a unit.  The
+// slices are the digits of the integer sum.  A single-block operand gets
+// exactly the scale and digits of the plain slicing.
+
+// Column maxima of every distinct block (tasks: prod = index of a term that
+// names the block, rows [k0, k1) of columns [c0, c0 + 64)).
+template <int NB>
+__global__ void __launch_bounds__(256) tc_termmax_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                         const Term* __restrict__ terms,
+                                                         const PrepTask* __restrict__ tasks,
+                                                         const int64_t* __restrict__ term_mx,
+                                                         unsigned long long* __restrict__ term_max) {
+    using TR = TileRegs<double>;
+    constexpr int NRED = 256 / TR::VPR;
+    __shared__ unsigned long long red[NRED][PT];
+    const PrepTask tk = tasks[blockIdx.x];
+    unsigned long long m[TR::VEC];
+#pragma unroll
+    for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
+    for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
+        TileRegs<double> R0, R1;
+        load_operand_regs<double>(bs, terms, tk.prod, 1, tk.k1, k, tk.c0, R0);
+        load_operand_regs<double>(bs, terms, tk.prod, 1, tk.k1, k + PT, tk.c0, R1);
+#pragma unroll
+        for (int j = 0; j < TR::VEC; ++j)
+#pragma unroll
+            for (int p = 0; p < TR::NPASS; ++p) {
+                const unsigned long long b0 = abs_bits(R0.v[p][j]), b1 = abs_bits(R1.v[p][j]);
+                const unsigned long long b = b0 > b1 ? b0 : b1;
+                m[j] = b > m[j] ? b : m[j];
+            }
+    }
+    const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
+    const int r0 = threadIdx.x / TR::VPR;
+#pragma unroll
+    for (int j = 0; j < TR::VEC; ++j) red[r0][vc + j] = m[j];
+    __syncthreads();
+    if (threadIdx.x < PT) {
+        const int col = threadIdx.x;
+        unsigned long long mx = red[0][col];
+#pragma unroll
+        for (int i = 1; i < NRED; ++i) mx = red[i][col] > mx ? red[i][col] : mx;
+        if (mx != 0) atomicMax(term_max + term_mx[tk.prod] + tk.c0 + col, mx);
+    }
+}
+
+// Parts of one 64 (K) x 64 (column) tile of a leaf operand (as
+// tc_prep_kernel), the operand formed in fixed point.  The block with k0 == 0
+// of each column strip also records the column scales (as FP64 bit patterns
+// whose exponent gives E) for the GEMM epilogue.
+template <int NB>
+__global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                            const LeafProduct* __restrict__ prods,
+                                                            const Term* __restrict__ terms,
+                                                            const TcProd* __restrict__ tcp,
+                                                            const PrepTask* __restrict__ tasks,
+                                                            const int64_t* __restrict__ term_mx,
+                                                            const unsigned long long* __restrict__ term_max) {
+    using G = Geo<MODE_OZAKI>;
+    using TR = TileRegs<double>;
+    constexpr int S = G::PARTS;
+    __shared__ long long tile[PT][PT + 1];
+    __shared__ int colE[PT];
+    const PrepTask tk = tasks[blockIdx.x];
+    const LeafProduct& lp = prods[tk.prod];
+    const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
+    if (threadIdx.x < PT) {
+        const int c = tk.c0 + threadIdx.x;
+        int emax = 0, cnt = 0;
+        bool nonfinite = false;
+        for (int t = 0; t < nt; ++t) {
+            if (c >= terms[t0 + t].cols) continue;
+            const unsigned long long mx = term_max[term_mx[t0 + t] + c];
+            if (mx == 0) continue;
+            const int e = col_exponent<G::HEAD>(mx);
+            nonfinite |= e >= kNonFinite;
+            emax = cnt == 0 ? e : max(emax, e);
+            ++cnt;
+        }
+        const int E = nonfinite ? kNonFinite : cnt > 1 ? emax + (32 - __clz(cnt - 1)) : emax;
+        colE[threadIdx.x] = E;
+        if (tk.k0 == 0) {
+            const unsigned long long bits = cnt == 0   ? 0ull
+                                            : nonfinite ? 0x7FF0000000000000ull
+                                                        : (unsigned long long)(E - G::HEAD + 1022) << 52;
+            (tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c] = bits;
+        }
+    }
+    __syncthreads();
+    {
+        const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
+        const int r0 = threadIdx.x / TR::VPR;
+        int Ec[TR::VEC];
+#pragma unroll
+        for (int j = 0; j < TR::VEC; ++j) Ec[j] = colE[vc + j];
+        long long acc[TR::NPASS][TR::VEC];
+#pragma unroll
+        for (int p = 0; p < TR::NPASS; ++p)
+#pragma unroll
+            for (int j = 0; j < TR::VEC; ++j) acc[p][j] = 0;
+        for (int t = 0; t < nt; ++t) {
+            TileRegs<double> R;
+            load_operand_regs<double>(bs, terms, t0 + t, 1, lp.K, tk.k0, tk.c0, R);  // signed term values
+#pragma unroll
+            for (int p = 0; p < TR::NPASS; ++p)
+#pragma unroll
+                for (int j = 0; j < TR::VEC; ++j) acc[p][j] += fixed_point<S>(R.v[p][j], Ec[j]);
+        }
+#pragma unroll
+        for (int p = 0; p < TR::NPASS; ++p)
+#pragma unroll
+            for (int j = 0; j < TR::VEC; ++j) tile[r0 + p * TR::RPP][vc + j] = acc[p][j];
+    }
+    __syncthreads();
+    const int rows_pad = tk.side ? lp.r_pad : lp.p_pad;
+    const Bind& b = bs.b[lp.inst];
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(b.W + (tk.side ? lp.tc_y_off : lp.tc_x_off));
+    const int64_t part_elems = (int64_t)rows_pad * lp.K_pad;
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        const int item = threadIdx.x + rep * 256;
+        const int col = item >> 3, kc = item & 7;
+        const int64_t base = (int64_t)(tk.c0 + col) * lp.K_pad + tk.k0 + kc * 8;
+        int dg[8][S];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) digits_of<S>(tile[kc * 8 + i][col], dg[i]);
+        store_parts<S>(dg, out, part_elems, base);
     }
 }
 
@@ -1265,11 +1420,20 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
     if (Geo<MODE>::SLICED) {
         cudaError_t e = cudaMemsetAsync(t.tc_ex, 0, t.tc_ex_bytes, s);
         if (e != cudaSuccess) return e;
+    }
+    if constexpr (MODE == MODE_OZAKI) {
+        // column maxima per distinct block, then operands formed in fixed point
         if (t.ncolmax > 0)
+            tc_termmax_kernel<NB><<<t.ncolmax, 256, 0, s>>>(bs, t.terms, t.colmax, t.term_mx, t.term_max);
+        if (t.nprep > 0)
+            tc_prep_fixed_kernel<NB>
+                <<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep, t.term_mx, t.term_max);
+    } else {
+        if (Geo<MODE>::SLICED && t.ncolmax > 0)
             tc_colmax_kernel<NB, typename PrepSrc<MODE>::T>
                 <<<t.ncolmax, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.colmax);
+        if (t.nprep > 0) tc_prep_kernel<NB, MODE><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
     }
-    if (t.nprep > 0) tc_prep_kernel<NB, MODE><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep);
     if (before_gemm) {
         cudaError_t e = cudaEventRecordWithFlags(before_gemm, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
@@ -1446,8 +1610,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
                 pt.k1 = k0 + PT;
                 prep.push_back(pt);
             }
-            // column maxima over the valid rows only
-            for (int k0 = 0; k0 < lp.K; k0 += kColSpan) {
+            // column maxima over the valid rows only (per operand; the FP64
+            // emulation takes them per distinct block below)
+            for (int k0 = 0; k0 < lp.K && h.leaf != LEAF_OZAKI; k0 += kColSpan) {
                 PrepTask ct{};
                 ct.prod = b.prod;
                 ct.side = (int8_t)b.side;
@@ -1458,14 +1623,49 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
             }
         }
     }
-    // device blob: TcProd[] | PrepTask[] (slicing) | PrepTask[] (maxima) | status | exponent maxima
+    // FP64 emulation: one column-maximum array per distinct block that some
+    // operand sums (terms naming the same block of the same buffer share it)
+    std::vector<int64_t> term_mx(h.terms.size(), -1);
+    int64_t tm_elems = 0;
+    if (h.leaf == LEAF_OZAKI) {
+        std::map<std::tuple<int, int, int64_t, int64_t, int, int>, int64_t> blocks;
+        for (const auto& key : order) {
+            const Buf& b = bufs[key];
+            const LeafProduct& lp = h.prods[b.prod];
+            const int t0 = b.side ? lp.y0 : lp.x0, nt = b.side ? lp.ny : lp.nx;
+            for (int t = t0; t < t0 + nt; ++t) {
+                const Term& tm = h.terms[t];
+                const auto bk = std::make_tuple((int)tm.inst, (int)tm.buf, (int64_t)tm.off, (int64_t)tm.ld,
+                                                (int)tm.rows, (int)tm.cols);
+                auto it = blocks.find(bk);
+                if (it == blocks.end()) {
+                    it = blocks.emplace(bk, tm_elems).first;
+                    tm_elems += (tm.cols + PT - 1) / PT * PT;
+                    for (int c0 = 0; c0 < tm.cols; c0 += PT)
+                        for (int k0 = 0; k0 < tm.rows; k0 += kColSpan) {
+                            PrepTask ct{};
+                            ct.prod = t;  // a term naming the block
+                            ct.c0 = c0;
+                            ct.k0 = k0;
+                            ct.k1 = std::min(k0 + kColSpan, (int)tm.rows);
+                            colmax.push_back(ct);
+                        }
+                }
+                term_mx[t] = it->second;
+            }
+        }
+    }
+    // device blob: TcProd[] | PrepTask[] (slicing) | PrepTask[] (maxima) | term offsets | status |
+    // exponent maxima of the operands, then of the blocks (zeroed per run)
     auto al = [](int64_t x) { return (x + 255) / 256 * 256; };
     const int64_t o_tp = 0;
     const int64_t o_prep = al(o_tp + (int64_t)np * sizeof(TcProd));
     const int64_t o_colmax = al(o_prep + (int64_t)prep.size() * sizeof(PrepTask));
-    const int64_t o_status = al(o_colmax + (int64_t)colmax.size() * sizeof(PrepTask));
+    const int64_t o_tmx = al(o_colmax + (int64_t)colmax.size() * sizeof(PrepTask));
+    const int64_t o_status = al(o_tmx + (int64_t)term_mx.size() * 8);
     const int64_t o_ex = al(o_status + 256);
-    const int64_t total = al(o_ex + std::max<int64_t>(ex_elems, 1) * 8);
+    const int64_t ex_total = std::max<int64_t>(ex_elems + tm_elems, 1);
+    const int64_t total = al(o_ex + ex_total * 8);
     char* blob = nullptr;
     if (cudaMalloc(&blob, total) != cudaSuccess) {
         cudaGetLastError();
@@ -1479,6 +1679,7 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     if (np) std::memcpy(hb.data() + o_tp, tp.data(), np * sizeof(TcProd));
     if (!prep.empty()) std::memcpy(hb.data() + o_prep, prep.data(), prep.size() * sizeof(PrepTask));
     if (!colmax.empty()) std::memcpy(hb.data() + o_colmax, colmax.data(), colmax.size() * sizeof(PrepTask));
+    if (!term_mx.empty()) std::memcpy(hb.data() + o_tmx, term_mx.data(), term_mx.size() * 8);
     cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
@@ -1491,8 +1692,10 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     d->colmax = reinterpret_cast<PrepTask*>(blob + o_colmax);
     d->ncolmax = (int)colmax.size();
     d->status = reinterpret_cast<int*>(blob + o_status);
+    d->term_mx = reinterpret_cast<int64_t*>(blob + o_tmx);
+    d->term_max = reinterpret_cast<unsigned long long*>(blob + o_ex) + ex_elems;
     d->tc_ex = blob + o_ex;
-    d->tc_ex_bytes = (size_t)std::max<int64_t>(ex_elems, 1) * 8;
+    d->tc_ex_bytes = (size_t)ex_total * 8;
     return ATA_OK;
 }
 

@@ -81,8 +81,10 @@ struct DeviceTables {
     TcProd* tcp = nullptr;
     PrepTask* prep = nullptr;
     int nprep = 0;
-    PrepTask* colmax = nullptr;  // column-maximum strips (sliced modes)
+    PrepTask* colmax = nullptr;  // column-maximum strips (sliced modes; FP64 emulation: per distinct block)
     int ncolmax = 0;
+    int64_t* term_mx = nullptr;              // FP64 emulation: per term, its block's maxima offset
+    unsigned long long* term_max = nullptr;  // ... the blocks' column maxima (bit patterns)
     int* status = nullptr;     // device error word of the tensor-core kernels
     char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
     size_t tc_ex_bytes = 0;

@@ -45,18 +45,21 @@ Rates rates_for(ata_dtype d) {
 
 // Bytes the operand preparation of the tensor-core leaves moves: every
 // distinct leaf operand (operands with equal terms share one part buffer)
-// element is read twice (column maxima, slicing) and written as its parts.
+// reads its terms twice (column maxima, slicing) and writes its parts.
 double prep_bytes(const Plan& P) {
     if (P.leaf == LEAF_F64) return 0.0;
     const TcGeom g = tc_geom(P.leaf);
     const double in = P.in_dt == DT_F64 ? 8.0 : 4.0;
-    double elems = 0;
+    // a fused operand sum reads each of its nt terms in both passes
+    double bytes = 0;
     std::set<int64_t> seen;
     for (const LeafProduct& lp : P.products) {
-        if (seen.insert(lp.tc_x_off).second) elems += (double)lp.K_pad * lp.p_pad;
-        if (lp.out_kind != OUT_SYRK && seen.insert(lp.tc_y_off).second) elems += (double)lp.K_pad * lp.r_pad;
+        if (seen.insert(lp.tc_x_off).second)
+            bytes += (double)lp.K_pad * lp.p_pad * (2.0 * in * lp.nx + g.parts * g.elem);
+        if (lp.out_kind != OUT_SYRK && seen.insert(lp.tc_y_off).second)
+            bytes += (double)lp.K_pad * lp.r_pad * (2.0 * in * lp.ny + g.parts * g.elem);
     }
-    return elems * (2.0 * in + g.parts * g.elem);
+    return bytes;
 }
 
 constexpr int64_t kWorkspaceCap = int64_t(48) << 30;  // bytes
@@ -112,10 +115,15 @@ std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int>, int> g_
 }  // namespace
 
 int default_fuse_levels(ata_dtype dtype, int variant) {
-    (void)variant;
     // FP64: additions run on the same FP64 pipe as the leaf DFMAs, so sums
     // recomputed per tile cost more than materialising them once.
-    if (dtype == ATA_F64 || dtype == ATA_F64_OZAKI) return 0;
+    if (dtype == ATA_F64) return 0;
+    // The FP64 emulation forms the bottom level's operand sums in fixed point
+    // while slicing them.  Their scale is bounded from the blocks' maxima, one
+    // bit above the largest for a two-term Strassen sum; Winograd's chained
+    // sums (up to four terms) would lose two of the 48 bits, so its sums stay
+    // materialised in FP64 and sliced at their exact scale.
+    if (dtype == ATA_F64_OZAKI) return variant == ATA_WINOGRAD ? 0 : 1;
     return 1;
 }
 
@@ -151,6 +159,9 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
         if (!(r < 0 ? build_plan(m, n, t, &P, &err) : build_gemm_plan(m, n, r, t, &P, &err))) continue;
         if ((int64_t)P.products.size() > kMaxLeafProducts) continue;
         if (P.ws_bytes > kWorkspaceCap) continue;
+        bool terms_ok = true;
+        for (const LeafProduct& lp : P.products) terms_ok = terms_ok && lp.nx <= kMaxTerms && lp.ny <= kMaxTerms;
+        if (!terms_ok) continue;
         const double tm = model_time(P, dtype);
         if (tm < best) {
             best = tm;

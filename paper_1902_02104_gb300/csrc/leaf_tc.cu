@@ -44,6 +44,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <vector>
 
@@ -810,8 +811,9 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
 // slices are the digits of the integer sum.  A single-block operand gets
 // exactly the scale and digits of the plain slicing.
 
-// Column maxima of every distinct block (tasks: prod = index of a term that
-// names the block, rows [k0, k1) of columns [c0, c0 + 64)).
+// Column maxima of row segments of the operand blocks (tasks: prod = index
+// of the segment's term, rows [k0, k1) of columns [c0, c0 + 64); term_mx:
+// offset of each segment's maxima in term_max).
 template <int NB>
 __global__ void __launch_bounds__(256) tc_termmax_kernel(const __grid_constant__ BindSet<NB> bs,
                                                          const Term* __restrict__ terms,
@@ -863,6 +865,7 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
                                                             const TcProd* __restrict__ tcp,
                                                             const PrepTask* __restrict__ tasks,
                                                             const int64_t* __restrict__ term_mx,
+                                                            const int64_t* __restrict__ mx_list,
                                                             const unsigned long long* __restrict__ term_max) {
     using G = Geo<MODE_OZAKI>;
     using TR = TileRegs<double>;
@@ -878,7 +881,11 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
         bool nonfinite = false;
         for (int t = 0; t < nt; ++t) {
             if (c >= terms[t0 + t].cols) continue;
-            const unsigned long long mx = term_max[term_mx[t0 + t] + c];
+            unsigned long long mx = 0;  // the maximum over the block's row segments
+            for (int64_t a = term_mx[t0 + t]; mx_list[a] >= 0; ++a) {
+                const unsigned long long v = term_max[mx_list[a] + c];
+                mx = v > mx ? v : mx;
+            }
             if (mx == 0) continue;
             const int e = col_exponent<G::HEAD>(mx);
             nonfinite |= e >= kNonFinite;
@@ -959,6 +966,9 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
     constexpr int kbpc = G::KC / G::KBLK > 0 ? G::KC / G::KBLK : 1;
     constexpr bool HAS_F = G::FMIN <= G::FMAX;
     constexpr int NKS = G::KBLK / G::KSTEP;
+    // F chunks (drained per chunk) start FOFF stages after the D chunks, so
+    // that a D drain overlaps the F MMAs of two stages (see the MMA issuer)
+    constexpr int FOFF = (G::ND > 0 && HAS_F && !G::F_FINAL) ? kbpc / 2 : 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // lo halves of the running float-float sums, column pairs interleaved:
@@ -1052,7 +1062,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0 && rank == 0) {
-            uint32_t it = 0, chunk = 0, tcount = 0;
+            uint32_t it = 0, chunk = 0, fchunk = 0, tcount = 0;
             bool ok = true;
             for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
                 const LeafTile lt = tiles[t];
@@ -1062,18 +1072,15 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                         ok = false;
                         break;
                     }
+                    tc_fence_after();
                 }
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const bool first_in_chunk = (kb % kbpc) == 0;
-                    const bool last_in_chunk = (kb % kbpc) == kbpc - 1 || kb == nkb - 1;
+                    const int kr = kb % kbpc;
+                    const bool first_in_chunk = kr == 0;
+                    const bool last_in_chunk = kr == kbpc - 1 || kb == nkb - 1;
+                    const bool f_first = kb == 0 || (FOFF > 0 && kr == FOFF);
+                    const bool f_last = kr == (FOFF + kbpc - 1) % kbpc || kb == nkb - 1;
                     const uint32_t buf = chunk % G::DBUF;
-                    if (G::ND > 0 && first_in_chunk) {
-                        if (!mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
-                                           ERR_TIMEOUT_MMA)) {
-                            ok = false;
-                            break;
-                        }
-                    }
                     const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
                     if (!mbar_wait<CG>(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA)) {
                         ok = false;
@@ -1088,51 +1095,71 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                         return make_desc(st + G::PARTS * SH::X_BYTES + q * SH::Y_BYTES + ks * G::KSTEP * G::ELEM,
                                          G::SBO, G::SWZ);
                     };
-                    if constexpr (G::ND > 0) {
-                        // D group: order d into accumulator min(d, ND-1); each accumulator is
-                        // overwritten by its first MMA of the chunk
-                        bool fresh[3] = {first_in_chunk, first_in_chunk, first_in_chunk};
+                    // D group of this stage (waits for the drain of the previous D chunk)
+                    auto run_d = [&]() -> bool {
+                        if constexpr (G::ND > 0) {
+                            if (first_in_chunk) {
+                                if (!mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
+                                                   ERR_TIMEOUT_MMA))
+                                    return false;
+                                tc_fence_after();
+                            }
+                            // order d into accumulator min(d, ND-1); each accumulator is
+                            // overwritten by its first MMA of the chunk
+                            bool fresh[3] = {first_in_chunk, first_in_chunk, first_in_chunk};
 #pragma unroll
-                        for (int ord = 0; ord <= G::DMAX; ++ord) {
-                            const int acc = ord < G::ND - 1 ? ord : G::ND - 1;
-                            const uint32_t d = tmem + (buf * G::ND + acc) * 128;
+                            for (int ord = 0; ord <= G::DMAX; ++ord) {
+                                const int acc = ord < G::ND - 1 ? ord : G::ND - 1;
+                                const uint32_t d = tmem + (buf * G::ND + acc) * 128;
 #pragma unroll
-                            for (int a = 0; a <= ord; ++a) {
-                                if (a >= G::PARTS || ord - a >= G::PARTS) continue;
+                                for (int a = 0; a <= ord; ++a) {
+                                    if (a >= G::PARTS || ord - a >= G::PARTS) continue;
 #pragma unroll
-                                for (int ks = 0; ks < NKS; ++ks) {
-                                    umma<MODE, CG>(d, desc_a(a, ks), desc_b(ord - a, ks), SH::IDESC,
-                                                   fresh[acc] ? 0u : 1u);
-                                    fresh[acc] = false;
+                                    for (int ks = 0; ks < NKS; ++ks) {
+                                        umma<MODE, CG>(d, desc_a(a, ks), desc_b(ord - a, ks), SH::IDESC,
+                                                       fresh[acc] ? 0u : 1u);
+                                        fresh[acc] = false;
+                                    }
                                 }
                             }
+                            if (last_in_chunk) umma_commit<CG>(b_dfull + 8 * buf);
                         }
-                        if (last_in_chunk) umma_commit<CG>(b_dfull + 8 * buf);
-                    }
-                    if constexpr (HAS_F) {
-                        if (!G::F_FINAL && first_in_chunk) {
-                            if (!mbar_wait<CG>(b_fempty, (chunk & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
-                                ok = false;
-                                break;
+                        return true;
+                    };
+                    // F group of this stage (waits for the drain of the previous F chunk)
+                    auto run_f = [&]() -> bool {
+                        if constexpr (HAS_F) {
+                            if (!G::F_FINAL && f_first) {
+                                if (!mbar_wait<CG>(b_fempty, (fchunk & 1) ^ 1, status, ERR_TIMEOUT_MMA)) return false;
+                                tc_fence_after();
                             }
-                        }
-                        bool first = G::F_FINAL ? (kb == 0) : first_in_chunk;
+                            bool first = G::F_FINAL ? (kb == 0) : f_first;
 #pragma unroll
-                        for (int ord = G::FMIN; ord <= G::FMAX; ++ord)
+                            for (int ord = G::FMIN; ord <= G::FMAX; ++ord)
 #pragma unroll
-                            for (int a = 0; a <= ord; ++a) {
-                                if (a >= G::PARTS || ord - a >= G::PARTS) continue;
+                                for (int a = 0; a <= ord; ++a) {
+                                    if (a >= G::PARTS || ord - a >= G::PARTS) continue;
 #pragma unroll
-                                for (int ks = 0; ks < NKS; ++ks) {
-                                    umma<MODE, CG>(tmem + G::F_COL, desc_a(a, ks), desc_b(ord - a, ks), SH::IDESC,
-                                                   first ? 0u : 1u);
-                                    first = false;
+                                    for (int ks = 0; ks < NKS; ++ks) {
+                                        umma<MODE, CG>(tmem + G::F_COL, desc_a(a, ks), desc_b(ord - a, ks),
+                                                       SH::IDESC, first ? 0u : 1u);
+                                        first = false;
+                                    }
                                 }
-                            }
-                        if (!G::F_FINAL && last_in_chunk) umma_commit<CG>(b_ffull);
+                            if (!G::F_FINAL && f_last) umma_commit<CG>(b_ffull);
+                        }
+                        return true;
+                    };
+                    // While the D accumulators of the previous chunk drain, this
+                    // stage's F MMAs go first and keep the tensor pipe busy.
+                    const bool f_before_d = FOFF > 0 && first_in_chunk && kb != 0;
+                    if (f_before_d ? !(run_f() && run_d()) : !(run_d() && run_f())) {
+                        ok = false;
+                        break;
                     }
                     umma_commit<CG>(b_empty + 8 * s);  // stage reusable once these MMAs finish
                     if (last_in_chunk) ++chunk;
+                    if (f_last) ++fchunk;
                 }
                 if (!ok) break;
                 if constexpr (G::F_FINAL) umma_commit<CG>(b_ffull);
@@ -1153,67 +1180,27 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
         const int cq = e >> 2;               // column slice
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const int row = 32 * q + lane;
-        uint32_t chunk = 0, tcount = 0;
+        uint32_t chunk = 0, fchunk = 0, tcount = 0;
         bool ok = true;
         for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
             const LeafTile lt = tiles[t];
             const TcProd* pr = tcp + lt.prod;
             const int nkb = pr->K_pad / G::KBLK;
-            const int nchunks = (nkb + kbpc - 1) / kbpc;
             float hi[NCOL];
 #pragma unroll
             for (int c = 0; c < NCOL; ++c) hi[c] = 0.f;
             if constexpr (G::ND > 0) {
-                for (int ci = 0; ci < nchunks; ++ci, ++chunk) {
-                    const uint32_t buf = chunk % G::DBUF;
-                    if (!mbar_wait<CG>(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) {
-                        const uint32_t col = cq * NCOL + g * 16;
-#pragma unroll
-                        for (int c8 = 0; c8 < 16; c8 += 8) {
-                        // the accumulators' 8 columns in flight together, one wait
-                        uint32_t a0[8], a1[8], a2[8];
-                        tmem_ld8_async(tmem + lane_base + (buf * G::ND + 0) * 128 + col + c8, a0);
-                        tmem_ld8_async(tmem + lane_base + (buf * G::ND + 1) * 128 + col + c8, a1);
-                        if constexpr (G::ND > 2)
-                            tmem_ld8_async(tmem + lane_base + (buf * G::ND + 2) * 128 + col + c8, a2);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int cc = 0; cc < 8; cc += 2) {
-                            const int c = c8 + cc;
-                            // chunk value h + l (accumulator 0 is exact, the others are at
-                            // most ~2^-8 of it), added to (hi, lo) as a float-float sum and
-                            // renormalised so that |lo| stays within half an ulp of hi;
-                            // two columns per instruction
-                            f32x2 h, l, s2, e2;
-                            two_sum2(pk2(__uint_as_float(a0[cc]), __uint_as_float(a0[cc + 1])),
-                                     pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1])), h, l);
-                            if constexpr (G::ND > 2)
-                                l = add2(l, pk2(__uint_as_float(a2[cc]), __uint_as_float(a2[cc + 1])));
-                            f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
-                            two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]), h, s2, e2);
-                            e2 = add2(e2, add2(ci == 0 ? 0ull : *lp, l));
-                            const f32x2 hn = add2(s2, e2);  // Fast2Sum: |s2| >= |e2|
-                            *lp = sub2(e2, sub2(hn, s2));
-                            upk2(hn, hi[g * 16 + c], hi[g * 16 + c + 1]);
-                        }
-                        }
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        if constexpr (CG == 1)
-                            mbar_arrive(b_dempty + 8 * buf);
-                        else
-                            mbar_arrive_cluster(b_dempty_c + 8 * buf);
-                    }
-                    if constexpr (HAS_F && !G::F_FINAL) {
-                        if (!mbar_wait<CG>(b_ffull, chunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                // Drains in the order the MMA issuer commits them: stage dnext
+                // ends a D chunk, stage fnext an F chunk (the tile's last stage
+                // ends both: D first).  lo holds a value once the tile's first
+                // drain has written it.
+                bool lo_init = false;
+                int dnext = min(kbpc - 1, nkb - 1);
+                int fnext = HAS_F && !G::F_FINAL ? min((FOFF + kbpc - 1) % kbpc, nkb - 1) : nkb;
+                while (dnext < nkb || fnext < nkb) {
+                    if (dnext <= fnext) {
+                        const uint32_t buf = chunk % G::DBUF;
+                        if (!mbar_wait<CG>(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE)) {
                             ok = false;
                             break;
                         }
@@ -1221,23 +1208,78 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
 #pragma unroll
                         for (int g = 0; g < NG; ++g) {
                             const uint32_t col = cq * NCOL + g * 16;
-                            float f[16];
-                            tmem_ld16(tmem + lane_base + G::F_COL + col, f);
 #pragma unroll
-                            for (int c = 0; c < 16; c += 2) {
-                                f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
-                                *lp = add2(*lp, pk2(f[c], f[c + 1]));
+                            for (int c8 = 0; c8 < 16; c8 += 8) {
+                                // the accumulators' 8 columns in flight together, one wait
+                                uint32_t a0[8], a1[8], a2[8];
+                                tmem_ld8_async(tmem + lane_base + (buf * G::ND + 0) * 128 + col + c8, a0);
+                                tmem_ld8_async(tmem + lane_base + (buf * G::ND + 1) * 128 + col + c8, a1);
+                                if constexpr (G::ND > 2)
+                                    tmem_ld8_async(tmem + lane_base + (buf * G::ND + 2) * 128 + col + c8, a2);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int cc = 0; cc < 8; cc += 2) {
+                                    const int c = c8 + cc;
+                                    // chunk value h + l (accumulator 0 is exact, the others are at
+                                    // most ~2^-8 of it), added to (hi, lo) as a float-float sum and
+                                    // renormalised so that |lo| stays within half an ulp of hi;
+                                    // two columns per instruction
+                                    f32x2 h, l, s2, e2;
+                                    two_sum2(pk2(__uint_as_float(a0[cc]), __uint_as_float(a0[cc + 1])),
+                                             pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1])), h, l);
+                                    if constexpr (G::ND > 2)
+                                        l = add2(l, pk2(__uint_as_float(a2[cc]), __uint_as_float(a2[cc + 1])));
+                                    f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
+                                    two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]), h, s2, e2);
+                                    e2 = add2(e2, add2(lo_init ? *lp : 0ull, l));
+                                    const f32x2 hn = add2(s2, e2);  // Fast2Sum: |s2| >= |e2|
+                                    *lp = sub2(e2, sub2(hn, s2));
+                                    upk2(hn, hi[g * 16 + c], hi[g * 16 + c + 1]);
+                                }
                             }
                         }
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) {
                             if constexpr (CG == 1)
-                                mbar_arrive(b_fempty);
+                                mbar_arrive(b_dempty + 8 * buf);
                             else
-                                mbar_arrive_cluster(b_fempty_c);
+                                mbar_arrive_cluster(b_dempty_c + 8 * buf);
                         }
+                        ++chunk;
+                        dnext = dnext == nkb - 1 ? nkb : min(dnext + kbpc, nkb - 1);
+                    } else {
+                        if constexpr (HAS_F && !G::F_FINAL) {
+                            if (!mbar_wait<CG>(b_ffull, fchunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+#pragma unroll
+                            for (int g = 0; g < NG; ++g) {
+                                const uint32_t col = cq * NCOL + g * 16;
+                                float f[16];
+                                tmem_ld16(tmem + lane_base + G::F_COL + col, f);
+#pragma unroll
+                                for (int c = 0; c < 16; c += 2) {
+                                    f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
+                                    const f32x2 fv = pk2(f[c], f[c + 1]);
+                                    *lp = lo_init ? add2(*lp, fv) : fv;
+                                }
+                            }
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) {
+                                if constexpr (CG == 1)
+                                    mbar_arrive(b_fempty);
+                                else
+                                    mbar_arrive_cluster(b_fempty_c);
+                            }
+                            ++fchunk;
+                        }
+                        fnext = fnext == nkb - 1 ? nkb : min(fnext + kbpc, nkb - 1);
                     }
+                    lo_init = true;
                 }
                 if (!ok) break;
             }
@@ -1424,10 +1466,10 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
     if constexpr (MODE == MODE_OZAKI) {
         // column maxima per distinct block, then operands formed in fixed point
         if (t.ncolmax > 0)
-            tc_termmax_kernel<NB><<<t.ncolmax, 256, 0, s>>>(bs, t.terms, t.colmax, t.term_mx, t.term_max);
+            tc_termmax_kernel<NB><<<t.ncolmax, 256, 0, s>>>(bs, t.atom_terms, t.colmax, t.atom_mx, t.term_max);
         if (t.nprep > 0)
             tc_prep_fixed_kernel<NB>
-                <<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep, t.term_mx, t.term_max);
+                <<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep, t.term_mx, t.mx_list, t.term_max);
     } else {
         if (Geo<MODE>::SLICED && t.ncolmax > 0)
             tc_colmax_kernel<NB, typename PrepSrc<MODE>::T>
@@ -1623,36 +1665,107 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
             }
         }
     }
-    // FP64 emulation: one column-maximum array per distinct block that some
-    // operand sums (terms naming the same block of the same buffer share it)
+    // FP64 emulation: the column maxima of every distinct block that some
+    // operand sums.  Blocks of one buffer with the same leading dimension,
+    // column offset and width differ only in their row ranges; the ranges are
+    // cut at every block boundary into disjoint row segments (atoms), each
+    // atom's maxima are taken once, and a block's maxima are the maxima over
+    // its atoms (a term's list of atom offsets, ended by -1).  Every element
+    // is then read once, however many blocks contain it.
     std::vector<int64_t> term_mx(h.terms.size(), -1);
+    std::vector<int64_t> mx_list;
+    std::vector<Term> atom_terms;
+    std::vector<int64_t> atom_mx;
     int64_t tm_elems = 0;
     if (h.leaf == LEAF_OZAKI) {
-        std::map<std::tuple<int, int, int64_t, int64_t, int, int>, int64_t> blocks;
+        // block: (inst, buf, dt, ld, column offset, cols) -> row ranges
+        using GKey = std::tuple<int, int, int, int64_t, int64_t, int>;
+        std::map<GKey, std::set<std::pair<int64_t, int64_t>>> groups;
+        auto gkey = [](const Term& tm) {
+            const int64_t ld = tm.ld > 0 ? tm.ld : 1;
+            const int64_t q = tm.off >= 0 ? tm.off / ld : (tm.off - ld + 1) / ld;  // floor
+            return std::make_pair(GKey{(int)tm.inst, (int)tm.buf, (int)tm.dt, ld, tm.off - q * ld, (int)tm.cols},
+                                  q);
+        };
+        std::vector<int> used_terms;
         for (const auto& key : order) {
             const Buf& b = bufs[key];
             const LeafProduct& lp = h.prods[b.prod];
             const int t0 = b.side ? lp.y0 : lp.x0, nt = b.side ? lp.ny : lp.nx;
             for (int t = t0; t < t0 + nt; ++t) {
                 const Term& tm = h.terms[t];
-                const auto bk = std::make_tuple((int)tm.inst, (int)tm.buf, (int64_t)tm.off, (int64_t)tm.ld,
-                                                (int)tm.rows, (int)tm.cols);
-                auto it = blocks.find(bk);
-                if (it == blocks.end()) {
-                    it = blocks.emplace(bk, tm_elems).first;
-                    tm_elems += (tm.cols + PT - 1) / PT * PT;
-                    for (int c0 = 0; c0 < tm.cols; c0 += PT)
-                        for (int k0 = 0; k0 < tm.rows; k0 += kColSpan) {
-                            PrepTask ct{};
-                            ct.prod = t;  // a term naming the block
-                            ct.c0 = c0;
-                            ct.k0 = k0;
-                            ct.k1 = std::min(k0 + kColSpan, (int)tm.rows);
-                            colmax.push_back(ct);
-                        }
-                }
-                term_mx[t] = it->second;
+                used_terms.push_back(t);
+                if (tm.rows <= 0 || tm.cols <= 0) continue;
+                const auto kq = gkey(tm);
+                groups[kq.first].insert({kq.second, kq.second + tm.rows});
             }
+        }
+        // atoms of each group: the segments between consecutive boundaries
+        // that some range covers
+        std::map<GKey, std::vector<std::pair<int64_t, int64_t>>> atoms_of;  // [q0, q1) -> ...
+        std::map<std::tuple<GKey, int64_t>, int64_t> atom_index;           // (group, q0) -> atom
+        for (const auto& g : groups) {
+            std::set<int64_t> cuts;
+            for (const auto& r : g.second) {
+                cuts.insert(r.first);
+                cuts.insert(r.second);
+            }
+            const std::vector<int64_t> cv(cuts.begin(), cuts.end());
+            for (size_t i = 0; i + 1 < cv.size(); ++i) {
+                const int64_t a = cv[i], z = cv[i + 1];
+                bool covered = false;
+                for (const auto& r : g.second) covered = covered || (r.first <= a && z <= r.second);
+                if (!covered) continue;
+                const GKey& k = g.first;
+                Term at{};
+                at.ld = std::get<3>(k);
+                at.off = a * at.ld + std::get<4>(k);
+                at.rows = (int32_t)(z - a);
+                at.cols = std::get<5>(k);
+                at.buf = (int8_t)std::get<1>(k);
+                at.dt = (int8_t)std::get<2>(k);
+                at.neg = 0;
+                at.inst = std::get<0>(k);
+                const int64_t id = (int64_t)atom_terms.size();
+                atom_terms.push_back(at);
+                atom_mx.push_back(tm_elems);
+                tm_elems += (at.cols + PT - 1) / PT * PT;
+                atom_index[{k, a}] = id;
+                atoms_of[k].push_back({a, z});
+                for (int c0 = 0; c0 < at.cols; c0 += PT)
+                    for (int k0 = 0; k0 < at.rows; k0 += kColSpan) {
+                        PrepTask ct{};
+                        ct.prod = (int32_t)id;  // an atom
+                        ct.c0 = c0;
+                        ct.k0 = k0;
+                        ct.k1 = std::min(k0 + kColSpan, at.rows);
+                        colmax.push_back(ct);
+                    }
+            }
+        }
+        // each term's list: the atoms inside its row range (blocks with equal
+        // ranges share one list)
+        std::map<std::tuple<GKey, int64_t, int64_t>, int64_t> lists;
+        for (int t : used_terms) {
+            if (term_mx[t] >= 0) continue;
+            const Term& tm = h.terms[t];
+            if (tm.rows <= 0 || tm.cols <= 0) {
+                term_mx[t] = (int64_t)mx_list.size();
+                mx_list.push_back(-1);
+                continue;
+            }
+            const auto kq = gkey(tm);
+            const auto lk = std::make_tuple(kq.first, kq.second, kq.second + tm.rows);
+            auto it = lists.find(lk);
+            if (it == lists.end()) {
+                const int64_t start = (int64_t)mx_list.size();
+                for (const auto& a : atoms_of[kq.first])
+                    if (kq.second <= a.first && a.second <= kq.second + tm.rows)
+                        mx_list.push_back(atom_mx[atom_index[{kq.first, a.first}]]);
+                mx_list.push_back(-1);
+                it = lists.emplace(lk, start).first;
+            }
+            term_mx[t] = it->second;
         }
     }
     // device blob: TcProd[] | PrepTask[] (slicing) | PrepTask[] (maxima) | term offsets | status |
@@ -1662,7 +1775,10 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     const int64_t o_prep = al(o_tp + (int64_t)np * sizeof(TcProd));
     const int64_t o_colmax = al(o_prep + (int64_t)prep.size() * sizeof(PrepTask));
     const int64_t o_tmx = al(o_colmax + (int64_t)colmax.size() * sizeof(PrepTask));
-    const int64_t o_status = al(o_tmx + (int64_t)term_mx.size() * 8);
+    const int64_t o_list = al(o_tmx + (int64_t)term_mx.size() * 8);
+    const int64_t o_aterm = al(o_list + (int64_t)mx_list.size() * 8);
+    const int64_t o_amx = al(o_aterm + (int64_t)atom_terms.size() * sizeof(Term));
+    const int64_t o_status = al(o_amx + (int64_t)atom_mx.size() * 8);
     const int64_t o_ex = al(o_status + 256);
     const int64_t ex_total = std::max<int64_t>(ex_elems + tm_elems, 1);
     const int64_t total = al(o_ex + ex_total * 8);
@@ -1680,6 +1796,10 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     if (!prep.empty()) std::memcpy(hb.data() + o_prep, prep.data(), prep.size() * sizeof(PrepTask));
     if (!colmax.empty()) std::memcpy(hb.data() + o_colmax, colmax.data(), colmax.size() * sizeof(PrepTask));
     if (!term_mx.empty()) std::memcpy(hb.data() + o_tmx, term_mx.data(), term_mx.size() * 8);
+    if (!mx_list.empty()) std::memcpy(hb.data() + o_list, mx_list.data(), mx_list.size() * 8);
+    if (!atom_terms.empty())
+        std::memcpy(hb.data() + o_aterm, atom_terms.data(), atom_terms.size() * sizeof(Term));
+    if (!atom_mx.empty()) std::memcpy(hb.data() + o_amx, atom_mx.data(), atom_mx.size() * 8);
     cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
@@ -1693,6 +1813,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     d->ncolmax = (int)colmax.size();
     d->status = reinterpret_cast<int*>(blob + o_status);
     d->term_mx = reinterpret_cast<int64_t*>(blob + o_tmx);
+    d->mx_list = reinterpret_cast<int64_t*>(blob + o_list);
+    d->atom_terms = reinterpret_cast<Term*>(blob + o_aterm);
+    d->atom_mx = reinterpret_cast<int64_t*>(blob + o_amx);
     d->term_max = reinterpret_cast<unsigned long long*>(blob + o_ex) + ex_elems;
     d->tc_ex = blob + o_ex;
     d->tc_ex_bytes = (size_t)ex_total * 8;

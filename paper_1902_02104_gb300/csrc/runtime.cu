@@ -219,6 +219,10 @@ void DeviceTables::free_all() {
     tc_blob = nullptr;
     tcp = nullptr;
     prep = nullptr;
+    colmax = nullptr;
+    term_mx = mx_list = atom_mx = nullptr;
+    atom_terms = nullptr;
+    term_max = nullptr;
     status = nullptr;
 }
 

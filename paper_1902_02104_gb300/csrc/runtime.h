@@ -83,8 +83,11 @@ struct DeviceTables {
     int nprep = 0;
     PrepTask* colmax = nullptr;  // column-maximum strips (sliced modes; FP64 emulation: per distinct block)
     int ncolmax = 0;
-    int64_t* term_mx = nullptr;              // FP64 emulation: per term, its block's maxima offset
-    unsigned long long* term_max = nullptr;  // ... the blocks' column maxima (bit patterns)
+    int64_t* term_mx = nullptr;              // FP64 emulation: per term, the start of its list in mx_list
+    int64_t* mx_list = nullptr;              // ... maxima offsets of the row segments of a block, -1 ended
+    Term* atom_terms = nullptr;              // ... the row segments (disjoint blocks of the buffers)
+    int64_t* atom_mx = nullptr;              // ... per segment, its maxima offset in term_max
+    unsigned long long* term_max = nullptr;  // ... the segments' column maxima (bit patterns)
     int* status = nullptr;     // device error word of the tensor-core kernels
     char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
     size_t tc_ex_bytes = 0;

@@ -854,60 +854,70 @@ __global__ void __launch_bounds__(256) tc_termmax_kernel(const __grid_constant__
     }
 }
 
+// Column scales of the operands (tasks: one per 64-column strip of every
+// distinct operand): E(c) from the maxima of the operand's blocks, stored as
+// an integer for the slicing kernel and as FP64 bits (whose exponent gives E)
+// for the GEMM epilogue.
+__global__ void __launch_bounds__(PT) tc_scale_kernel(const LeafProduct* __restrict__ prods,
+                                                      const Term* __restrict__ terms,
+                                                      const TcProd* __restrict__ tcp,
+                                                      const PrepTask* __restrict__ tasks,
+                                                      const int64_t* __restrict__ term_mx,
+                                                      const int64_t* __restrict__ mx_list,
+                                                      const unsigned long long* __restrict__ term_max,
+                                                      int* __restrict__ col_e) {
+    using G = Geo<MODE_OZAKI>;
+    const PrepTask tk = tasks[blockIdx.x];
+    const LeafProduct& lp = prods[tk.prod];
+    const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
+    const int c = tk.c0 + threadIdx.x;
+    int emax = 0, cnt = 0;
+    bool nonfinite = false;
+    for (int t = 0; t < nt; ++t) {
+        if (c >= terms[t0 + t].cols) continue;
+        unsigned long long mx = 0;  // the maximum over the block's row segments
+        for (int64_t a = term_mx[t0 + t]; mx_list[a] >= 0; ++a) {
+            const unsigned long long v = term_max[mx_list[a] + c];
+            mx = v > mx ? v : mx;
+        }
+        if (mx == 0) continue;
+        const int e = col_exponent<G::HEAD>(mx);
+        nonfinite |= e >= kNonFinite;
+        emax = cnt == 0 ? e : max(emax, e);
+        ++cnt;
+    }
+    const int E = nonfinite ? kNonFinite : cnt > 1 ? emax + (32 - __clz(cnt - 1)) : emax;
+    const TcProd& tp = tcp[tk.prod];
+    col_e[(tk.side ? tp.ey_index : tp.ex_index) + c] = E;
+    const unsigned long long bits = cnt == 0   ? 0ull
+                                    : nonfinite ? 0x7FF0000000000000ull
+                                                : (unsigned long long)(E - G::HEAD + 1022) << 52;
+    (tk.side ? tp.ey : tp.ex)[c] = bits;
+}
+
 // Parts of one 64 (K) x 64 (column) tile of a leaf operand (as
-// tc_prep_kernel), the operand formed in fixed point.  The block with k0 == 0
-// of each column strip also records the column scales (as FP64 bit patterns
-// whose exponent gives E) for the GEMM epilogue.
+// tc_prep_kernel), the operand formed in fixed point at the column scales
+// that tc_scale_kernel computed.
 template <int NB>
 __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constant__ BindSet<NB> bs,
                                                             const LeafProduct* __restrict__ prods,
                                                             const Term* __restrict__ terms,
                                                             const TcProd* __restrict__ tcp,
                                                             const PrepTask* __restrict__ tasks,
-                                                            const int64_t* __restrict__ term_mx,
-                                                            const int64_t* __restrict__ mx_list,
-                                                            const unsigned long long* __restrict__ term_max) {
-    using G = Geo<MODE_OZAKI>;
+                                                            const int* __restrict__ col_e) {
     using TR = TileRegs<double>;
-    constexpr int S = G::PARTS;
+    constexpr int S = Geo<MODE_OZAKI>::PARTS;
     __shared__ long long tile[PT][PT + 1];
-    __shared__ int colE[PT];
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
-    if (threadIdx.x < PT) {
-        const int c = tk.c0 + threadIdx.x;
-        int emax = 0, cnt = 0;
-        bool nonfinite = false;
-        for (int t = 0; t < nt; ++t) {
-            if (c >= terms[t0 + t].cols) continue;
-            unsigned long long mx = 0;  // the maximum over the block's row segments
-            for (int64_t a = term_mx[t0 + t]; mx_list[a] >= 0; ++a) {
-                const unsigned long long v = term_max[mx_list[a] + c];
-                mx = v > mx ? v : mx;
-            }
-            if (mx == 0) continue;
-            const int e = col_exponent<G::HEAD>(mx);
-            nonfinite |= e >= kNonFinite;
-            emax = cnt == 0 ? e : max(emax, e);
-            ++cnt;
-        }
-        const int E = nonfinite ? kNonFinite : cnt > 1 ? emax + (32 - __clz(cnt - 1)) : emax;
-        colE[threadIdx.x] = E;
-        if (tk.k0 == 0) {
-            const unsigned long long bits = cnt == 0   ? 0ull
-                                            : nonfinite ? 0x7FF0000000000000ull
-                                                        : (unsigned long long)(E - G::HEAD + 1022) << 52;
-            (tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c] = bits;
-        }
-    }
-    __syncthreads();
     {
         const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
         const int r0 = threadIdx.x / TR::VPR;
+        const int* ce = col_e + (tk.side ? tcp[tk.prod].ey_index : tcp[tk.prod].ex_index) + tk.c0 + vc;
         int Ec[TR::VEC];
 #pragma unroll
-        for (int j = 0; j < TR::VEC; ++j) Ec[j] = colE[vc + j];
+        for (int j = 0; j < TR::VEC; ++j) Ec[j] = __ldg(ce + j);
         long long acc[TR::NPASS][TR::VEC];
 #pragma unroll
         for (int p = 0; p < TR::NPASS; ++p)
@@ -1464,12 +1474,15 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
         if (e != cudaSuccess) return e;
     }
     if constexpr (MODE == MODE_OZAKI) {
-        // column maxima per distinct block, then operands formed in fixed point
+        // column maxima per row segment, column scales, then operands formed in
+        // fixed point
         if (t.ncolmax > 0)
             tc_termmax_kernel<NB><<<t.ncolmax, 256, 0, s>>>(bs, t.atom_terms, t.colmax, t.atom_mx, t.term_max);
+        if (t.nscale > 0)
+            tc_scale_kernel<<<t.nscale, PT, 0, s>>>(t.prods, t.terms, t.tcp, t.scale, t.term_mx, t.mx_list,
+                                                     t.term_max, t.col_e);
         if (t.nprep > 0)
-            tc_prep_fixed_kernel<NB>
-                <<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep, t.term_mx, t.mx_list, t.term_max);
+            tc_prep_fixed_kernel<NB><<<t.nprep, 256, 0, s>>>(bs, t.prods, t.terms, t.tcp, t.prep, t.col_e);
     } else {
         if (Geo<MODE>::SLICED && t.ncolmax > 0)
             tc_colmax_kernel<NB, typename PrepSrc<MODE>::T>
@@ -1639,10 +1652,18 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
             if (side == 1 || syrk) t.ey_index = it->second.ex_index;
         }
     }
+    std::vector<PrepTask> scale;  // FP64 emulation: column-scale strips
     for (const auto& key : order) {
         const Buf& b = bufs[key];
         const LeafProduct& lp = h.prods[b.prod];
         for (int c0 = 0; c0 < b.rows_used; c0 += PT) {
+            if (h.leaf == LEAF_OZAKI) {
+                PrepTask st{};
+                st.prod = b.prod;
+                st.side = (int8_t)b.side;
+                st.c0 = c0;
+                scale.push_back(st);
+            }
             for (int k0 = 0; k0 < lp.K_pad; k0 += PT) {
                 PrepTask pt{};
                 pt.prod = b.prod;
@@ -1665,6 +1686,13 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
             }
         }
     }
+    // Slicing tasks ordered by tile position: operands summed from the same
+    // blocks (the operand sums of one Strassen node, a diagonal leaf's column
+    // block and the node's quadrants) read the same source tiles at the same
+    // (k0, c0), which then come from L2 for all but the first of them.
+    std::stable_sort(prep.begin(), prep.end(), [](const PrepTask& a, const PrepTask& b) {
+        return a.k0 != b.k0 ? a.k0 < b.k0 : a.c0 < b.c0;
+    });
     // FP64 emulation: the column maxima of every distinct block that some
     // operand sums.  Blocks of one buffer with the same leading dimension,
     // column offset and width differ only in their row ranges; the ranges are
@@ -1732,8 +1760,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
                 tm_elems += (at.cols + PT - 1) / PT * PT;
                 atom_index[{k, a}] = id;
                 atoms_of[k].push_back({a, z});
-                for (int c0 = 0; c0 < at.cols; c0 += PT)
-                    for (int k0 = 0; k0 < at.rows; k0 += kColSpan) {
+                // strips side by side over the same rows run together
+                for (int k0 = 0; k0 < at.rows; k0 += kColSpan)
+                    for (int c0 = 0; c0 < at.cols; c0 += PT) {
                         PrepTask ct{};
                         ct.prod = (int32_t)id;  // an atom
                         ct.c0 = c0;
@@ -1778,7 +1807,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     const int64_t o_list = al(o_tmx + (int64_t)term_mx.size() * 8);
     const int64_t o_aterm = al(o_list + (int64_t)mx_list.size() * 8);
     const int64_t o_amx = al(o_aterm + (int64_t)atom_terms.size() * sizeof(Term));
-    const int64_t o_status = al(o_amx + (int64_t)atom_mx.size() * 8);
+    const int64_t o_scale = al(o_amx + (int64_t)atom_mx.size() * 8);
+    const int64_t o_cole = al(o_scale + (int64_t)scale.size() * sizeof(PrepTask));
+    const int64_t o_status = al(o_cole + (h.leaf == LEAF_OZAKI ? ex_elems * 4 : 0));
     const int64_t o_ex = al(o_status + 256);
     const int64_t ex_total = std::max<int64_t>(ex_elems + tm_elems, 1);
     const int64_t total = al(o_ex + ex_total * 8);
@@ -1800,6 +1831,7 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     if (!atom_terms.empty())
         std::memcpy(hb.data() + o_aterm, atom_terms.data(), atom_terms.size() * sizeof(Term));
     if (!atom_mx.empty()) std::memcpy(hb.data() + o_amx, atom_mx.data(), atom_mx.size() * 8);
+    if (!scale.empty()) std::memcpy(hb.data() + o_scale, scale.data(), scale.size() * sizeof(PrepTask));
     cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blob);
@@ -1816,6 +1848,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     d->mx_list = reinterpret_cast<int64_t*>(blob + o_list);
     d->atom_terms = reinterpret_cast<Term*>(blob + o_aterm);
     d->atom_mx = reinterpret_cast<int64_t*>(blob + o_amx);
+    d->scale = reinterpret_cast<PrepTask*>(blob + o_scale);
+    d->nscale = (int)scale.size();
+    d->col_e = reinterpret_cast<int*>(blob + o_cole);
     d->term_max = reinterpret_cast<unsigned long long*>(blob + o_ex) + ex_elems;
     d->tc_ex = blob + o_ex;
     d->tc_ex_bytes = (size_t)ex_total * 8;

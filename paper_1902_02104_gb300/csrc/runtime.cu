@@ -221,6 +221,8 @@ void DeviceTables::free_all() {
     prep = nullptr;
     colmax = nullptr;
     term_mx = mx_list = atom_mx = nullptr;
+    scale = nullptr;
+    col_e = nullptr;
     atom_terms = nullptr;
     term_max = nullptr;
     status = nullptr;
@@ -444,11 +446,13 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     out->n_combine_tasks = (int32_t)nc;
     // kernels one execution launches: a split and a combine kernel per level,
     // then the leaf kernel, preceded for tensor-core leaves by the operand
-    // preparation (and the column maxima of the sliced modes)
-    const int leaf_kernels = P.products.empty() ? 0
-                             : P.leaf == LEAF_F64 ? 1
-                             : P.leaf == LEAF_TF32 ? 2
-                                                   : 3;
+    // preparation (and the column maxima of the sliced modes, and the column
+    // scales of the FP64 emulation)
+    const int leaf_kernels = P.products.empty()    ? 0
+                             : P.leaf == LEAF_F64   ? 1
+                             : P.leaf == LEAF_TF32  ? 2
+                             : P.leaf == LEAF_OZAKI ? 4
+                                                    : 3;
     out->n_launches = (int32_t)(P.split_levels.size() + P.combine_levels.size() + leaf_kernels);
     out->mults = P.stats.mults;
     out->classical_mults = P.m * P.n * (P.n + 1) / 2;  // A^t A: the upper triangle

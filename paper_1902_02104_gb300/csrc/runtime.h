@@ -88,6 +88,9 @@ struct DeviceTables {
     Term* atom_terms = nullptr;              // ... the row segments (disjoint blocks of the buffers)
     int64_t* atom_mx = nullptr;              // ... per segment, its maxima offset in term_max
     unsigned long long* term_max = nullptr;  // ... the segments' column maxima (bit patterns)
+    PrepTask* scale = nullptr;               // ... column-scale strips (one per 64 columns of an operand)
+    int nscale = 0;
+    int* col_e = nullptr;                    // ... column scales E(c), indexed like the column maxima
     int* status = nullptr;     // device error word of the tensor-core kernels
     char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
     size_t tc_ex_bytes = 0;

@@ -638,47 +638,42 @@ __global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ 
 
 // Balanced base-256 digits of v = round(x * 2^(8S - E)), most significant
 // first: x * 2^-E ~= sum_s d[s] * 2^(-8(s+1)), |d[0]| <= 256 >> HEAD (E
-// carries the column's headroom), d[s>0] in [-128, 127].  They are returned
+// carries the column's headroom), d[s>0] in [-128, 127].  They are kept
 // biased, b[s] = d[s] + 128: adding 128 to every base-256 position below the
 // top one turns the balanced digits into the plain bytes of u = v + bias
 // (each d[s] + 128 lies in [0, 255]), and the top digit is the arithmetic
-// shift of u.  Integer arithmetic only.
-// v = round(x * 2^(8S - E)) from the bits of x (integer arithmetic only); 0
-// for zero, subnormal and non-finite x or a non-finite column.
+// shift of u plus 128.  Integer arithmetic only.
+//
+// v from the bits of x: the significand shifted right by r, rounded to
+// nearest (ties up) as ((m >> (r - 1)) + 1) >> 1; 0 for zero, subnormal and
+// non-finite x and for a non-finite column (r > 63).
 template <int S>
 __device__ __forceinline__ long long fixed_point(double x, int E) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
+    const int r = E - 8 * S + 1075 - eb;  // right shift to units of 2^(E - 8S)
     long long v = 0;
-    if (eb != 0 && eb != 0x7FF && E < kNonFinite) {
+    if (eb != 0 && eb != 0x7FF) {
         const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
-        const int shift = (eb - 1075) + 8 * S - E;
-        if (shift >= 0)
-            v = m << shift;
-        else if (shift > -62)
-            v = (m + (1LL << (-shift - 1))) >> (-shift);
+        if (r <= 0)
+            v = m << -r;
+        else
+            v = ((m >> min(r - 1, 63)) + 1) >> 1;
         if (bits < 0) v = -v;
     }
     return v;
 }
 
-// Biased digits of a fixed-point value v (|v| <= 2^(8S) + a few units).
+// u = v + bias of a fixed-point value v (|v| <= 2^(8S) + a few units): the
+// biased digits of v are the bytes of u below the top one.
 template <int S>
-__device__ __forceinline__ void digits_of(long long v, int (&b)[S]) {
+__device__ __forceinline__ long long biased_value(long long v) {
     constexpr long long bias = (long long)(((unsigned long long)1 << (8 * (S - 1))) - 1) / 255 * 128;
-    const long long u = v + bias;
-#pragma unroll
-    for (int s = 1; s < S; ++s) b[s] = (int)((u >> (8 * (S - 1 - s))) & 255);
-    b[0] = (int)(u >> (8 * (S - 1))) + 128;
-}
-
-template <int S>
-__device__ __forceinline__ void biased_digits(double x, int E, int (&b)[S]) {
-    digits_of<S>(fixed_point<S>(x, E), b);
+    return v + bias;
 }
 
 // The same for an FP32 value and S = 3 (24 bits) in 32-bit integers.
-__device__ __forceinline__ void biased_digits(float x, int E, int (&b)[3]) {
+__device__ __forceinline__ long long biased_value_f32(float x, int E) {
     const unsigned int bits = __float_as_uint(x);
     const int eb = (int)((bits >> 23) & 0xFF);
     int v = 0;
@@ -691,28 +686,33 @@ __device__ __forceinline__ void biased_digits(float x, int E, int (&b)[3]) {
             v = (int)(((long long)m + (1LL << (-shift - 1))) >> (-shift));
         if (bits >> 31) v = -v;
     }
-    const int u = v + 0x8080;
-    b[2] = u & 255;
-    b[1] = (u >> 8) & 255;
-    b[0] = (u >> 16) + 128;
+    return (long long)(v + 0x8080);
 }
 
-// bf16 bit pattern of (b - 128) * 2^-8(s+1) for a biased digit b in
+// FP32 bits of (b - 128) * 2^-8(s+1) for biased digit b = b[s] of u, in
 // [-128, 384]: b is placed in the significand of 1.5 * 2^23 (exact integer
-// float), one FMA removes the offset and applies the power of two (exact: the
-// result has at most 9 significant bits), and the bf16 is the upper half of
-// the float's bits, exact since its low 16 bits are zero.
+// float; for s > 0 one byte permute inserts the byte of u), one FMA removes
+// the offset and applies the power of two (exact: the result has at most 9
+// significant bits), and the bf16 is the upper half of the float's bits,
+// exact since its low 16 bits are zero.
 __host__ __device__ constexpr float exp2_neg(int e) {
     float r = 1.0f;
     for (int i = 0; i < e; ++i) r *= 0.5f;
     return r;
 }
 
-template <int s>
-__device__ __forceinline__ uint32_t digit_f32_bits(int b) {
+template <int S, int s>
+__device__ __forceinline__ uint32_t digit_f32_bits(long long u) {
     constexpr float scale = exp2_neg(8 * (s + 1));
-    const float f = __int_as_float(0x4B400000 + b);  // 12582912 + b
-    return __float_as_uint(fmaf(f, scale, -12583040.0f * scale));  // (12582912 + 128) * scale
+    uint32_t fb;
+    if constexpr (s == 0) {
+        fb = 0x4B400000u + 128u + (uint32_t)(int)(u >> (8 * (S - 1)));
+    } else {
+        constexpr int byte = S - 1 - s;  // position of digit s in u
+        const uint32_t w = byte < 4 ? (uint32_t)u : (uint32_t)((unsigned long long)u >> 32);
+        fb = __byte_perm(w, 0x4B400000u, 0x7650u + (byte & 3));  // 0x4B4000bb
+    }
+    return __float_as_uint(fmaf(__uint_as_float(fb), scale, -12583040.0f * scale));  // (12582912 + 128) * scale
 }
 
 // Two bf16 (the upper halves of lo's and hi's float bits) in one 32-bit word,
@@ -730,18 +730,19 @@ struct PrepSrc<MODE_OZAKI> {
     using T = double;
 };
 
-// Writes the S parts of 8 consecutive K values of one column: part s gets
-// the 8 bf16 of digit s, 16 bytes at out + s * part_elems + base.
+// Writes the S parts of 8 consecutive K values of one column (their biased
+// values u): part s gets the 8 bf16 of digit s, 16 bytes at
+// out + s * part_elems + base.
 template <int S, int s = 0>
-__device__ __forceinline__ void store_parts(const int (&dg)[8][S], __nv_bfloat16* out, int64_t part_elems,
+__device__ __forceinline__ void store_parts(const long long (&u)[8], __nv_bfloat16* out, int64_t part_elems,
                                             int64_t base) {
     uint4 q;
-    q.x = pack_bf16_hi(digit_f32_bits<s>(dg[0][s]), digit_f32_bits<s>(dg[1][s]));
-    q.y = pack_bf16_hi(digit_f32_bits<s>(dg[2][s]), digit_f32_bits<s>(dg[3][s]));
-    q.z = pack_bf16_hi(digit_f32_bits<s>(dg[4][s]), digit_f32_bits<s>(dg[5][s]));
-    q.w = pack_bf16_hi(digit_f32_bits<s>(dg[6][s]), digit_f32_bits<s>(dg[7][s]));
+    q.x = pack_bf16_hi(digit_f32_bits<S, s>(u[0]), digit_f32_bits<S, s>(u[1]));
+    q.y = pack_bf16_hi(digit_f32_bits<S, s>(u[2]), digit_f32_bits<S, s>(u[3]));
+    q.z = pack_bf16_hi(digit_f32_bits<S, s>(u[4]), digit_f32_bits<S, s>(u[5]));
+    q.w = pack_bf16_hi(digit_f32_bits<S, s>(u[6]), digit_f32_bits<S, s>(u[7]));
     *reinterpret_cast<uint4*>(out + s * part_elems + base) = q;
-    if constexpr (s + 1 < S) store_parts<S, s + 1>(dg, out, part_elems, base);
+    if constexpr (s + 1 < S) store_parts<S, s + 1>(u, out, part_elems, base);
 }
 
 // Parts of one 64 (K) x 64 (column) tile of a leaf operand, written K-major:
@@ -787,11 +788,16 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ Bi
             const unsigned long long mx =
                 reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
             const int E = col_exponent<Geo<MODE>::HEAD>(mx);
-            int dg[8][S];
+            long long u[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) biased_digits(tile[kc * 8 + i][col], E, dg[i]);
+            for (int i = 0; i < 8; ++i) {
+                if constexpr (sizeof(TS) == 8)
+                    u[i] = biased_value<S>(fixed_point<S>(tile[kc * 8 + i][col], E));
+                else
+                    u[i] = biased_value_f32(tile[kc * 8 + i][col], E);
+            }
             __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(parts);
-            store_parts<S>(dg, out, part_elems, base);
+            store_parts<S>(u, out, part_elems, base);
         }
     }
 }
@@ -946,10 +952,10 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
         const int item = threadIdx.x + rep * 256;
         const int col = item >> 3, kc = item & 7;
         const int64_t base = (int64_t)(tk.c0 + col) * lp.K_pad + tk.k0 + kc * 8;
-        int dg[8][S];
+        long long u[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) digits_of<S>(tile[kc * 8 + i][col], dg[i]);
-        store_parts<S>(dg, out, part_elems, base);
+        for (int i = 0; i < 8; ++i) u[i] = biased_value<S>(tile[kc * 8 + i][col]);
+        store_parts<S>(u, out, part_elems, base);
     }
 }
 

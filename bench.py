@@ -389,15 +389,21 @@ def run_ours(args):
     err = sampled_error(oracle, A_np, C, n, err_kind, dev, torch, count=cnt)
     dev_status = plan.device_status()
 
-    # end to end through the C ABI from pinned host memory
+    # end to end through the C ABI from pinned host memory: every step copies
+    # its input in and its packed result out.  The steps are pipelined calls
+    # (the copies of one step overlap the executions of its neighbours on two
+    # staging sets); the clock stops when the last result is on the host.
     A_host = torch.from_numpy(A_np).pin_memory()
     C_host = torch.empty(n * (n + 1) // 2, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    ata.ata_execute_host(plan, A_host.numpy(), C_host.numpy(), stream)
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):  # both staging sets' graphs captured
+        ata.ata_execute_host_async(plan, A_host.numpy(), C_host.numpy())
+    ata.ata_plan_wait(plan)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ata.ata_execute_host(plan, A_host.numpy(), C_host.numpy(), stream)
+        ata.ata_execute_host_async(plan, A_host.numpy(), C_host.numpy())
+    ata.ata_plan_wait(plan)
     t_e2e = (time.perf_counter() - t0) / e2e_steps
     t_e2e = max_over_ranks(torch, t_e2e, world)
 
@@ -432,7 +438,8 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
                      "kernel": kern, "flops_per_launch": leaf_flops},
         "e2e": {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_np.nbytes),
-                "d2h_bytes_per_step": int(C.numel() * 8)},
+                "d2h_bytes_per_step": int(C.numel() * 8), "steps": e2e_steps,
+                "calls": "ata_execute_host_async per step (pipelined), ata_plan_wait at the end"},
         "gpu_launches": int(args.steps * info["n_launches"]),
         "clocks": clocks,
     }

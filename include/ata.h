@@ -198,6 +198,27 @@ ata_status ata_execute(ata_plan plan, const void* A, int64_t lda,
 ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda,
                             double* C_packed_host, void* stream);
 
+/* Pipelined end-to-end execution for a stream of inputs: queues the copy of
+ * A_host (host memory, leading dimension lda) to the device, the execution
+ * and the copy of the packed result to C_packed_host on streams the plan
+ * owns, and returns without waiting.  Successive calls alternate between two
+ * device staging sets (allocated on first use: 2 x (m n + n(n+1)/2)
+ * elements), so that the copies of one call overlap the executions of its
+ * neighbours; executions run one at a time in call order.  Host buffers
+ * should be pinned (page-locked) for the copies to overlap.  A_host may not
+ * be modified, and C_packed_host not read, until ata_plan_wait returns; a
+ * plan's pipelined calls come from one thread at a time and are not mixed
+ * with other executions of the same plan before ata_plan_wait.
+ * Errors: as ata_execute_host; errors of the queued work are reported by
+ * ata_plan_wait. */
+ata_status ata_execute_host_async(ata_plan plan, const void* A_host,
+                                  int64_t lda, double* C_packed_host);
+
+/* Waits until every call queued by ata_execute_host_async on plan has
+ * finished (ATA_OK at once if there was none).  Errors: ATA_EINVAL (NULL
+ * plan), ATA_ECUDA (a queued copy or execution failed). */
+ata_status ata_plan_wait(ata_plan plan);
+
 /* Many independent products in one queued batch: plans[i] (each built for
  * its own m_i x n_i and dtype) applied to A[i] (device, leading dimension
  * lda[i]) into C_packed[i].  All leaf tiles of all instances run in one

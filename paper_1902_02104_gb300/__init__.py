@@ -18,6 +18,7 @@ from . import build as _build
 __all__ = [
     "ATA_F64", "ATA_F32_BF16X3", "ATA_F32_TF32", "ATA_F64_OZAKI", "ATA_STRASSEN", "ATA_WINOGRAD",
     "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
+    "ata_execute_host_async", "ata_plan_wait",
     "ata_execute_batched", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
     "packed_size", "lib_path",
 ]
@@ -88,6 +89,8 @@ def load():
         "ata_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "ata_execute": ([vp, vp, i64, dp, vp], i32),
         "ata_execute_host": ([vp, vp, i64, dp, vp], i32),
+        "ata_execute_host_async": ([vp, vp, i64, dp], i32),
+        "ata_plan_wait": ([vp], i32),
         "ata_execute_batched": ([ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                  ctypes.POINTER(vp), vp], i32),
         "ata_plan_destroy": ([vp], None),
@@ -315,6 +318,30 @@ def ata_execute_host(plan: Plan, A, C=None, stream=None):
     _check(load().ata_execute_host(plan.handle, ctypes.c_void_p(A_np.ctypes.data), max(plan.n, 1),
                                    ctypes.c_void_p(C_np.ctypes.data), _stream_handle(stream)))
     return C
+
+
+def ata_execute_host_async(plan: Plan, A, C=None):
+    """Pipelined end to end from host memory: queues the copy-in, execution
+    and copy-out and returns C at once.  A must stay unmodified, and C
+    unread, until ata_plan_wait(plan); both should be pinned."""
+    import numpy as np
+    A_np = A.numpy() if hasattr(A, "numpy") and not isinstance(A, np.ndarray) else A
+    want = np.float64 if plan.dtype in (ATA_F64, ATA_F64_OZAKI) else np.float32
+    if A_np.dtype != want or A_np.shape != (plan.m, plan.n) or not A_np.flags.c_contiguous:
+        raise ValueError(f"A must be a C-contiguous {want.__name__} array of shape ({plan.m}, {plan.n})")
+    if C is None:
+        C = np.empty(packed_size(plan.n), dtype=np.float64)
+    C_np = C.numpy() if hasattr(C, "numpy") and not isinstance(C, np.ndarray) else C
+    if C_np.dtype != np.float64 or C_np.size != packed_size(plan.n) or not C_np.flags.c_contiguous:
+        raise ValueError("C must be a contiguous float64 array of n(n+1)/2 entries")
+    _check(load().ata_execute_host_async(plan.handle, ctypes.c_void_p(A_np.ctypes.data), max(plan.n, 1),
+                                         ctypes.c_void_p(C_np.ctypes.data)))
+    return C
+
+
+def ata_plan_wait(plan: Plan):
+    """Wait for every call queued by ata_execute_host_async on plan."""
+    _check(load().ata_plan_wait(plan.handle))
 
 
 def ata_execute_batched(plans, As, Cs=None, stream=None):

@@ -355,6 +355,45 @@ ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, Gr
 // ===========================================================================
 using namespace ata;
 
+// Pipelined host execution (ata_execute_host_async): two device staging sets
+// used alternately, the copy-in, execution and copy-out of a call on three
+// streams ordered by events, and one graph per staging set.
+struct HostPipe {
+    bool ready = false;
+    cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+    cudaEvent_t a_ready[2] = {nullptr, nullptr};    // staging A[b] holds the call's input
+    cudaEvent_t comp_done[2] = {nullptr, nullptr};  // the execution on set b has finished
+    cudaEvent_t c_read[2] = {nullptr, nullptr};     // C[b] has been copied out
+    void* A[2] = {nullptr, nullptr};
+    double* C[2] = {nullptr, nullptr};
+    GraphCache graph[2];
+    uint64_t calls = 0;
+    void sync() const {
+        for (cudaStream_t s : {h2d, comp, d2h})
+            if (s) cudaStreamSynchronize(s);
+    }
+    void release() {
+        sync();
+        for (int b = 0; b < 2; ++b) {
+            graph[b].release();
+            for (cudaEvent_t* e : {&a_ready[b], &comp_done[b], &c_read[b]}) {
+                if (*e) cudaEventDestroy(*e);
+                *e = nullptr;
+            }
+            if (A[b]) cudaFree(A[b]);
+            if (C[b]) cudaFree(C[b]);
+            A[b] = nullptr;
+            C[b] = nullptr;
+        }
+        for (cudaStream_t* s : {&h2d, &comp, &d2h}) {
+            if (*s) cudaStreamDestroy(*s);
+            *s = nullptr;
+        }
+        ready = false;
+        calls = 0;
+    }
+};
+
 struct ata_plan_s {
     uint64_t id = 0;
     Plan plan;
@@ -370,7 +409,9 @@ struct ata_plan_s {
     // staging for ata_execute_host
     void* stage_A = nullptr;
     double* stage_C = nullptr;
+    HostPipe pipe;  // ata_execute_host_async
     ~ata_plan_s() {
+        pipe.release();
         graph.release();
         tables.free_all();
         if (ws) cudaFree(ws);
@@ -491,6 +532,8 @@ ata_status rebuild_tables(ata_plan plan, int64_t lda, int64_t ldb = 0, int64_t l
     plan->ldb = ldb;
     plan->ldc = ldc;
     plan->graph.release();
+    plan->pipe.graph[0].release();
+    plan->pipe.graph[1].release();
     return ATA_OK;
 }
 
@@ -498,6 +541,21 @@ ata_status check_ptr(const void* p, int align, const char* what) {
     if (reinterpret_cast<uintptr_t>(p) % align != 0)
         return fail(ATA_EINVAL, std::string(what) + " is not aligned to its element size");
     return ATA_OK;
+}
+
+// One execution of an A^t A plan on `s` through graph cache g (arguments
+// checked by the caller).
+ata_status execute_on(ata_plan plan, const void* A, int64_t lda, double* C_packed, cudaStream_t s, GraphCache* g) {
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (lda != plan->lda) {
+        // the streams may still run the previous tables
+        ATA_CUDA(cudaStreamSynchronize(s));
+        plan->pipe.sync();
+        ata_status st = rebuild_tables(plan, lda);
+        if (st != ATA_OK) return st;
+    }
+    Bind b = make_bind(plan, A, lda, C_packed);
+    return launch_via_graph(plan->tables, &b, 1, g, s);
 }
 
 }  // namespace
@@ -841,15 +899,7 @@ ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_pack
     st = check_ptr(C_packed, 8, "C_packed");
     if (st != ATA_OK) return st;
     if (n == 0) return ATA_OK;
-    std::lock_guard<std::mutex> lk(plan->mu);
-    if (lda != plan->lda) {
-        // the stream may still run the previous tables
-        ATA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-        st = rebuild_tables(plan, lda);
-        if (st != ATA_OK) return st;
-    }
-    Bind b = make_bind(plan, A, lda, C_packed);
-    return launch_via_graph(plan->tables, &b, 1, &plan->graph, static_cast<cudaStream_t>(stream));
+    return execute_on(plan, A, lda, C_packed, static_cast<cudaStream_t>(stream), &plan->graph);
 }
 
 ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, double* C_host, void* stream) {
@@ -886,6 +936,67 @@ ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, doub
     if (st != ATA_OK) return st;
     ATA_CUDA(cudaMemcpyAsync(C_host, plan->stage_C, (size_t)(n * (n + 1) / 2) * 8, cudaMemcpyDeviceToHost, s));
     ATA_CUDA(cudaStreamSynchronize(s));
+    return ATA_OK;
+}
+
+ata_status ata_execute_host_async(ata_plan plan, const void* A_host, int64_t lda, double* C_host) {
+    if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan: use ata_gemm_tn");
+    const int64_t m = plan->plan.m, n = plan->plan.n;
+    const int es = elem_bytes(plan->dtype);
+    if (lda < n || lda < 1) return fail(ATA_EINVAL, "lda must be >= max(n, 1)");
+    if (m > 0 && n > 0 && !A_host) return fail(ATA_EINVAL, "A is NULL");
+    if (n > 0 && !C_host) return fail(ATA_EINVAL, "C_packed is NULL");
+    if (n == 0) return ATA_OK;
+    HostPipe& P = plan->pipe;
+    const size_t a_bytes = (size_t)m * n * es, c_bytes = (size_t)(n * (n + 1) / 2) * 8;
+    int b;
+    {
+        std::lock_guard<std::mutex> lk(plan->mu);
+        if (!P.ready) {
+            bool ok = true;
+            for (cudaStream_t* st : {&P.h2d, &P.comp, &P.d2h})
+                ok = ok && cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) == cudaSuccess;
+            for (int i = 0; i < 2 && ok; ++i) {
+                for (cudaEvent_t* e : {&P.a_ready[i], &P.comp_done[i], &P.c_read[i]})
+                    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+                ok = ok && (m == 0 || cudaMalloc(&P.A[i], a_bytes) == cudaSuccess);
+                ok = ok && cudaMalloc(&P.C[i], c_bytes) == cudaSuccess;
+            }
+            if (!ok) {
+                cudaGetLastError();
+                P.release();
+                return fail(ATA_ENOMEM, "pipelined host execution: streams, events or staging buffers");
+            }
+            P.ready = true;
+        }
+        b = (int)(P.calls++ & 1);
+    }
+    // copy-in, once the execution that last read staging set b has finished
+    ATA_CUDA(cudaStreamWaitEvent(P.h2d, P.comp_done[b], 0));
+    if (m > 0)
+        ATA_CUDA(cudaMemcpy2DAsync(P.A[b], (size_t)n * es, A_host, (size_t)lda * es, (size_t)n * es, (size_t)m,
+                                   cudaMemcpyHostToDevice, P.h2d));
+    ATA_CUDA(cudaEventRecord(P.a_ready[b], P.h2d));
+    // execution, once the input has arrived and the copy-out that last read
+    // C[b] has finished
+    ATA_CUDA(cudaStreamWaitEvent(P.comp, P.a_ready[b], 0));
+    ATA_CUDA(cudaStreamWaitEvent(P.comp, P.c_read[b], 0));
+    ata_status st = execute_on(plan, P.A[b] ? P.A[b] : (const void*)P.C[b], n, P.C[b], P.comp, &P.graph[b]);
+    if (st != ATA_OK) return st;
+    ATA_CUDA(cudaEventRecord(P.comp_done[b], P.comp));
+    // copy-out
+    ATA_CUDA(cudaStreamWaitEvent(P.d2h, P.comp_done[b], 0));
+    ATA_CUDA(cudaMemcpyAsync(C_host, P.C[b], c_bytes, cudaMemcpyDeviceToHost, P.d2h));
+    ATA_CUDA(cudaEventRecord(P.c_read[b], P.d2h));
+    return ATA_OK;
+}
+
+ata_status ata_plan_wait(ata_plan plan) {
+    if (!plan) return fail(ATA_EINVAL, "plan is NULL");
+    const HostPipe& P = plan->pipe;
+    if (!P.ready) return ATA_OK;
+    for (cudaStream_t s : {P.h2d, P.comp, P.d2h}) ATA_CUDA(cudaStreamSynchronize(s));
     return ATA_OK;
 }
 

@@ -1,6 +1,6 @@
 """Parity of the FP64 path (ATA_F64) with the oracle, through the C ABI.
 
-Tolerance (BASELINE config 1/2): max_ij |C - C_ref| / (|A|^t|A|)_ij <= 1e-11.
+Tolerance (FP64 accuracy): max_ij |C - C_ref| / (|A|^t|A|)_ij <= 1e-11.
 Exact-integer inputs must match bitwise (every product and partial sum is an
 integer below 2^53, so any summation order gives the same doubles).
 """
@@ -159,8 +159,8 @@ def sample_indices(n, count, seed, cuts=()):
 
 @pytest.mark.parametrize("m,n", [(5000, 5000), (10000, 10000), (20000, 8000)])
 def test_paper_scale_sampled(gpu, m, n):
-    """BASELINE config 2 at the bench's launch configuration (autotuned
-    cutoff): sampled entries against the oracle, plus invariants."""
+    """Paper-scale square and tall inputs at the bench's launch configuration
+    (autotuned cutoff): sampled entries against the oracle, plus invariants."""
     import torch
     A_np = inputs.normal(m, n, seed=1)
     plan = ata.Plan(m, n, ata.ATA_F64, 0)

@@ -1,7 +1,7 @@
 """Parity of the tensor-core leaves (bf16x3, TF32, FP64 emulation) with the
 oracle, through the C ABI.
 
-Tolerances (BASELINE config 3): normwise ||C - C_ref||_F / ||C_ref||_F <=
+Tolerances (FP32 accuracy): normwise ||C - C_ref||_F / ||C_ref||_F <=
 1e-6 for bf16x3 and <= 1e-3 for TF32, where C_ref is the FP64 product of the
 FP32-rounded input; the FP64-emulation leaf (ATA_F64_OZAKI) keeps the FP64
 componentwise bound max |C - C_ref| / (|A|^t|A|) <= 1e-11.
@@ -124,8 +124,8 @@ def sampled_normwise(A_np, C, n, count, seed):
 
 
 @pytest.mark.parametrize("dtype", MODES32)
-def test_config3_full_size_sampled(gpu, dtype):
-    """16384 x 8192 FP32, every 8th column x 1e3 (BASELINE config 3), at the
+def test_fp32_workload_full_size_sampled(gpu, dtype):
+    """16384 x 8192 FP32, every 8th column x 1e3 (the FP32 workload), at the
     bench's cutoff: sampled normwise error within the stated bound."""
     import torch
     A_np = inputs.scaled_cols(16384, 8192, seed=2)

@@ -153,6 +153,51 @@ def sampled_error(oracle, A_np, C, n, kind, dev, torch, count=2000, seed=123):
     return float(np.sqrt(num / den))
 
 
+def library_reference(A, A_np, n, eff, kind, oracle, dev, torch, reps=2, count=2000, seed=123):
+    """torch.matmul(A^t, A) on the same resident input, the library reference
+    point (cuBLAS: a float64 GEMM for FP64 input, a float32 GEMM with TF32 off
+    for FP32 input).  It computes the full n x n product (2 m n^2 FLOP, the
+    same effective count).  Sampled error against the oracle as for ours."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        out = torch.matmul(A.t(), A)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = torch.matmul(A.t(), A)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    rng = np.random.default_rng(seed)  # the entries sampled_error takes
+    I = rng.integers(0, n, size=count)
+    J = rng.integers(0, n, size=count)
+    I, J = np.minimum(I, J), np.maximum(I, J)
+
+    def entries(i, j):
+        return out[torch.from_numpy(i).to(dev), torch.from_numpy(j).to(dev)].double().cpu().numpy()
+
+    if kind == "componentwise":
+        err = oracle.componentwise_error(entries(I, J), oracle.ata_entries(A_np, I, J),
+                                         oracle.ata_entries(A_np, I, J, absval=True))
+    else:
+        keep = I != J
+        I, J = I[keep], J[keep]
+        d = np.arange(n)
+        ref_d, ref_o = oracle.ata_entries(A_np, d, d), oracle.ata_entries(A_np, I, J)
+        w = (n * (n - 1) / 2) / max(I.size, 1) * 2.0
+        num = np.sum((entries(d, d) - ref_d) ** 2) + w * np.sum((entries(I, J) - ref_o) ** 2)
+        err = float(np.sqrt(num / (np.sum(ref_d ** 2) + w * np.sum(ref_o ** 2))))
+    del out
+    torch.cuda.empty_cache()
+    return {"call": f"torch.matmul(A.t(), A), {str(A.dtype).replace('torch.', '')}, TF32 off", "ms": ms,
+            "value": eff / (ms / 1e3) / 1e12, "unit": "TFLOP/s", kind + "_sampled": err, "samples": count}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -466,6 +511,8 @@ def run_ours(args):
         line["speedup_vs_plain_f64"] = fms / ms_max
         del pf
         torch.cuda.empty_cache()
+    if not args.no_library:
+        line["library_reference"] = library_reference(A, A_np, n, eff, err_kind, oracle, dev, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_sample(A_np, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {
@@ -783,6 +830,26 @@ def run_gemm(args):
                    "h2d_bytes_per_step": int(X_np.nbytes + Y_np.nbytes), "d2h_bytes_per_step": int(p * r * 8)}
     line["gpu_launches"] = int(args.steps * info["n_launches"])
     line["clocks"] = clocks
+    if not args.no_library:
+        # torch.matmul(X^t, Y) on the same resident inputs (cuBLAS, TF32 off)
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        out = torch.matmul(X.t(), Y)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(2):
+            out = torch.matmul(X.t(), Y)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        lms = e0.elapsed_time(e1) / 2
+        lgot = out[torch.from_numpy(I).to(dev), torch.from_numpy(J).to(dev)].double().cpu().numpy()
+        lerr = float(np.max(np.abs(lgot - ref) / G)) if kind == "componentwise" else \
+            float(np.linalg.norm(lgot - ref) / np.linalg.norm(ref))
+        line["library_reference"] = {"call": f"torch.matmul(X.t(), Y), {str(X.dtype).replace('torch.', '')}, "
+                                             f"TF32 off", "ms": lms, "value": eff / (lms / 1e3) / 1e12,
+                                     "unit": "TFLOP/s", kind: lerr, "samples": 2000}
+        del out
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample of entries (about --cpu-budget
         # seconds), extrapolated to all p r entries
@@ -818,6 +885,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(GEMM_WORKLOADS) + EXTRA_WORKLOADS,
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-library", action="store_true", help="skip the torch.matmul library reference")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

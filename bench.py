@@ -617,7 +617,7 @@ def run_batched(args, mode):
     line["e2e"] = {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s",
                    "h2d_bytes_per_step": int(sum(a.nbytes for a in mats)),
                    "d2h_bytes_per_step": int(sum(c.numel() * 8 for c in Cs))}
-    line["gpu_launches"] = None
+    line["gpu_launches"] = int(args.steps * ata.ata_batched_graph_kernels(plans, As))
     line["clocks"] = clocks
     if rank == 0:
         print(json.dumps(line))
@@ -664,6 +664,7 @@ def run_serving(args, mode):
         srv.poll(t, 600_000_000)
     wall = time.perf_counter() - t0
     st = srv.stats()
+    served_kernels = srv.kernels()
     eff = sum(effective_flops(*pool[i].shape) for i in which)
     # latency of the timed requests only: the server keeps all; recompute from the tail
     kind, tol = TOLERANCE[mode]
@@ -717,7 +718,7 @@ def run_serving(args, mode):
     line["error"] = {kind + "_max_of_4": max(errs), "tolerance": tol}
     line["roofline"] = None
     line["e2e"] = None
-    line["gpu_launches"] = None
+    line["gpu_launches"] = int(served_kernels)
     if rank == 0:
         print(json.dumps(line))
     return 0

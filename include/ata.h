@@ -241,6 +241,17 @@ ata_status ata_execute_batched(const ata_plan* plans, int count,
 ata_status ata_plan_enable_stage_timing(ata_plan plan, int enable);
 ata_status ata_plan_stage_times(ata_plan plan, float* ms);
 
+/* Kernel launches one execution of the plan makes: the kernel nodes of its
+ * captured CUDA graph (the graph of its most recent ata_execute).  Errors:
+ * ATA_EINVAL (NULL argument, or the plan has not been executed yet). */
+ata_status ata_plan_graph_kernels(ata_plan plan, int32_t* kernels);
+
+/* The same for ata_execute_batched(plans, count, ..., lda, ...): the kernel
+ * nodes of the graphs of all its groups of instances.  Errors: ATA_EINVAL
+ * (NULL or invalid argument, or the batch has not been executed yet). */
+ata_status ata_batched_graph_kernels(const ata_plan* plans, int count,
+                                     const int64_t* lda, int32_t* kernels);
+
 /* Error word of the plan's tensor-core kernels (0 = none).  Their waits on
  * pipeline barriers are bounded (1 s); a wait that gives up records a
  * nonzero code (1 TMA producer, 2 MMA issuer, 3 epilogue), the kernel
@@ -351,8 +362,14 @@ ata_status ata_poll(ata_server srv, ata_ticket ticket, int timeout_us);
 ata_status ata_server_stats(ata_server srv, double* p50_us, double* p99_us,
                             int64_t* completed);
 
-/* Forget the latencies recorded so far (e.g. after a warm-up phase). */
+/* Forget the latencies recorded so far (e.g. after a warm-up phase), and
+ * the kernel count below. */
 ata_status ata_server_reset_stats(ata_server srv);
+
+/* Kernel launches of the executions the server has queued since it was
+ * created or its statistics were reset (each execution: the kernel nodes of
+ * its plan's graph, as ata_plan_graph_kernels).  Errors: ATA_EINVAL. */
+ata_status ata_server_kernels(ata_server srv, int64_t* kernels);
 
 /* Stop the scheduler after draining queued work, then free everything. */
 void ata_server_destroy(ata_server srv);

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "ATA_F64", "ATA_F32_BF16X3", "ATA_F32_TF32", "ATA_F64_OZAKI", "ATA_STRASSEN", "ATA_WINOGRAD",
     "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
-    "ata_execute_host_async", "ata_plan_wait",
+    "ata_execute_host_async", "ata_plan_wait", "ata_batched_graph_kernels",
     "ata_execute_batched", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
     "packed_size", "lib_path",
 ]
@@ -96,6 +96,9 @@ def load():
         "ata_plan_destroy": ([vp], None),
         "ata_execute_static_scratch": ([i64, i64, vp, i64, dp, i32, vp], i32),
         "ata_plan_device_status": ([vp, ctypes.POINTER(ctypes.c_int)], i32),
+        "ata_plan_graph_kernels": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
+        "ata_batched_graph_kernels": ([ctypes.POINTER(vp), i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)],
+                                      i32),
         "ata_plan_enable_stage_timing": ([vp, i32], i32),
         "ata_plan_stage_times": ([vp, ctypes.POINTER(ctypes.c_float)], i32),
         "ata_server_create": ([ctypes.POINTER(vp), ctypes.c_size_t, i32, i32], i32),
@@ -105,6 +108,7 @@ def load():
                               ctypes.POINTER(i64)], i32),
         "ata_server_destroy": ([vp], None),
         "ata_server_reset_stats": ([vp], i32),
+        "ata_server_kernels": ([vp, ctypes.POINTER(i64)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -182,6 +186,12 @@ class Plan:
         c = ctypes.c_int()
         _check(load().ata_plan_device_status(self.handle, ctypes.byref(c)))
         return c.value
+
+    def graph_kernels(self) -> int:
+        """Kernel launches one execution makes (nodes of the captured graph)."""
+        k = ctypes.c_int32()
+        _check(load().ata_plan_graph_kernels(self.handle, ctypes.byref(k)))
+        return k.value
 
     def enable_stage_timing(self, enable: bool = True):
         _check(load().ata_plan_enable_stage_timing(self.handle, int(enable)))
@@ -320,6 +330,16 @@ def ata_execute_host(plan: Plan, A, C=None, stream=None):
     return C
 
 
+def ata_batched_graph_kernels(plans, As) -> int:
+    """Kernel launches one ata_execute_batched(plans, As) makes (after it has run)."""
+    count = len(plans)
+    ph = (ctypes.c_void_p * count)(*[p.handle for p in plans])
+    ld = (ctypes.c_int64 * count)(*[_check_A(p, A) for p, A in zip(plans, As)])
+    k = ctypes.c_int32()
+    _check(load().ata_batched_graph_kernels(ph, count, ld, ctypes.byref(k)))
+    return k.value
+
+
 def ata_execute_host_async(plan: Plan, A, C=None):
     """Pipelined end to end from host memory: queues the copy-in, execution
     and copy-out and returns C at once.  A must stay unmodified, and C
@@ -410,6 +430,12 @@ class Server:
 
     def reset_stats(self):
         _check(load().ata_server_reset_stats(self.handle))
+
+    def kernels(self) -> int:
+        """Kernel launches of the executions queued since creation or the last reset."""
+        k = ctypes.c_int64()
+        _check(load().ata_server_kernels(self.handle, ctypes.byref(k)))
+        return k.value
 
     def close(self):
         if getattr(self, "handle", None):

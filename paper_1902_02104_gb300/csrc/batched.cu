@@ -116,3 +116,26 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
     }
     return ATA_OK;
 }
+
+extern "C" ata_status ata_batched_graph_kernels(const ata_plan* plans, int count, const int64_t* lda,
+                                               int32_t* kernels) {
+    if (!kernels || count < 0 || (count > 0 && (!plans || !lda))) return fail(ATA_EINVAL, "NULL or invalid argument");
+    *kernels = 0;
+    std::vector<int64_t> key;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return fail(ATA_EINVAL, "NULL plan in batch");
+        key.push_back((int64_t)plan_id(plans[i]));
+        key.push_back(lda[i]);
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    int32_t total = 0;
+    for (int g0 = 0; g0 < count; g0 += kMaxBatchBind) {
+        const int g1 = std::min(count, g0 + kMaxBatchBind);
+        auto it = g_batches.find(std::vector<int64_t>(key.begin() + 2 * g0, key.begin() + 2 * g1));
+        if (it == g_batches.end() || !it->second->graph.exec)
+            return fail(ATA_EINVAL, "this batch has not been executed yet");
+        total += it->second->graph.kernels;
+    }
+    *kernels = total;
+    return ATA_OK;
+}

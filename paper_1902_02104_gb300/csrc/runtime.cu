@@ -296,6 +296,23 @@ ata_status capture_graph(const DeviceTables& t, const Bind* binds, int nb, Graph
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    {
+        // kernel nodes of the captured work (the launches one replay makes)
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(cudaGetLastError(), "cudaGraphGetNodes");
+        }
+        std::vector<cudaGraphNode_t> nodes(nn);
+        int kernels = 0;
+        if (nn > 0 && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
+            for (size_t i = 0; i < nn; ++i) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+            }
+        }
+        g->kernels = kernels;
+    }
     if (g->exec) {
         cudaGraphExecUpdateResultInfo info;
         if (cudaGraphExecUpdate(g->exec, graph, &info) == cudaSuccess) {
@@ -324,6 +341,7 @@ void GraphCache::release() {
     exec = nullptr;
     cap_stream = nullptr;
     binds.clear();
+    kernels = 0;
     timed_run = false;
 }
 
@@ -1017,6 +1035,14 @@ ata_status ata_plan_stage_times(ata_plan plan, float* ms) {
     if (!plan->graph.timing || !plan->graph.timed_run || !plan->graph.ev[0])
         return fail(ATA_EINVAL, "stage timing is not enabled or nothing has run");
     for (int i = 0; i < 4; ++i) ATA_CUDA(cudaEventElapsedTime(&ms[i], plan->graph.ev[i], plan->graph.ev[i + 1]));
+    return ATA_OK;
+}
+
+ata_status ata_plan_graph_kernels(ata_plan plan, int32_t* kernels) {
+    if (!plan || !kernels) return fail(ATA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (!plan->graph.exec) return fail(ATA_EINVAL, "the plan has not been executed yet");
+    *kernels = plan->graph.kernels;
     return ATA_OK;
 }
 

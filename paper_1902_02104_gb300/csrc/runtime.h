@@ -103,6 +103,7 @@ struct GraphCache {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<Bind> binds;
+    int kernels = 0;            // kernel nodes of the captured graph
     bool timing = false;        // graph records ev[] around its stages
     bool timed_run = false;     // an execution with timing has been queued
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

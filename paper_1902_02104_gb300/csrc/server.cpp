@@ -79,6 +79,7 @@ struct ata_server_s {
     std::deque<Request> queue;
     std::unordered_map<ata_ticket, TicketInfo> tickets;
     std::vector<double> latencies_us;
+    int64_t kernels = 0;  // kernel launches of the executions queued since the last reset
     ata_ticket next_ticket = 1;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -213,6 +214,8 @@ struct ata_server_s {
                 e->busy = true;
                 ata_status st = ata_execute(e->plan, r.A, r.lda, r.C, free_slot->stream);
                 std::string emsg = st == ATA_OK ? std::string() : g_last_error;
+                int32_t nk = 0;
+                if (st == ATA_OK && ata_plan_graph_kernels(e->plan, &nk) == ATA_OK) kernels += nk;
                 if (st == ATA_OK && cudaEventRecord(free_slot->done, free_slot->stream) != cudaSuccess) {
                     st = ATA_ECUDA;
                     emsg = "cudaEventRecord failed";
@@ -338,6 +341,14 @@ ata_status ata_server_reset_stats(ata_server srv) {
     if (!srv) return fail(ATA_EINVAL, "server is NULL");
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->latencies_us.clear();
+    srv->kernels = 0;
+    return ATA_OK;
+}
+
+ata_status ata_server_kernels(ata_server srv, int64_t* kernels) {
+    if (!srv || !kernels) return fail(ATA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *kernels = srv->kernels;
     return ATA_OK;
 }
 

@@ -44,6 +44,9 @@ def test_null_plan_rejected_without_device_work():
     assert lib.ata_gemm_plan_create(None, 1, 1, 1, 0, None) == ata.ATA_EINVAL
     assert lib.ata_execute_host_async(None, None, 1, None) == ata.ATA_EINVAL
     assert lib.ata_plan_wait(None) == ata.ATA_EINVAL
+    assert lib.ata_plan_graph_kernels(None, None) == ata.ATA_EINVAL
+    assert lib.ata_batched_graph_kernels(None, -1, None, None) == ata.ATA_EINVAL
+    assert lib.ata_server_kernels(None, None) == ata.ATA_EINVAL
     assert b"NULL" in lib.ata_last_error_message() or lib.ata_last_error_message() != b""
 
 

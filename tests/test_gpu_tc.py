@@ -76,6 +76,21 @@ def test_ozaki_componentwise(gpu, m, n, cutoff):
     assert err <= 1e-11, err
 
 
+@pytest.mark.parametrize("m,n,cutoff", [(1600, 900, 128), (1000, 1000, 200)])
+def test_ozaki_row_bands_exact(gpu, m, n, cutoff):
+    # integers whose row bands differ by powers of two: the blocks that the
+    # Strassen operands sum (quadrants at several depths, column blocks) have
+    # column maxima that differ block to block, and the maxima of a block are
+    # assembled from its disjoint row segments.  Too small a column scale
+    # would overflow the fixed point; the result must be exact.
+    rng = np.random.default_rng(21)
+    A = rng.integers(-4, 5, size=(m, n)).astype(np.float64)
+    A *= np.exp2((np.arange(m) // 150 * 3) % 10)[:, None]  # |C| < 2^33: exact in every mode
+    C, plan = run(A, ata.ATA_F64_OZAKI, cutoff)
+    assert plan.info["max_strassen_levels"] >= 1
+    assert np.array_equal(C, oracle.ata_packed(A))
+
+
 def test_ozaki_wide_exponent_range(gpu):
     # columns spanning 2^-200 .. 2^200: the per-column scaling keeps each
     # classical leaf within the componentwise bound.  (Strassen sums mix

@@ -467,9 +467,44 @@ struct Shape {
     static constexpr int TAIL = CG == 2 && LO < Y_BYTES ? Y_BYTES : 0;
     static constexpr int SMEM = NSTAGE * STAGE + LO + 1024 /*align*/ + 256 /*barriers*/ + TAIL;
     static constexpr uint32_t IDESC = G::IDESC_KIND | ((128u >> 3) << 17) | ((128u * CG >> 4) << 24);
-    static constexpr int THREADS = 32 * (2 + G::EPI_WARPS);
+    static constexpr int THREADS = 32 * (3 + G::EPI_WARPS);  // TMA, MMA, epilogue warps, wait helper
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
+
+// Position of K block kb (of nkb) in the exact D chunks (kbpc blocks each)
+// and in the F chunks, which start FOFF blocks later.  f_before_d: a D chunk
+// starts here while an F chunk continues, so the stage's F MMAs are issued
+// before the wait for the previous D chunk's drain.
+struct StageFlags {
+    bool first_in_chunk, last_in_chunk, f_first, f_last, f_before_d;
+};
+template <int kbpc, int FOFF>
+__device__ __forceinline__ StageFlags stage_flags(int kb, int nkb) {
+    const int kr = kb % kbpc;
+    StageFlags f;
+    f.first_in_chunk = kr == 0;
+    f.last_in_chunk = kr == kbpc - 1 || kb == nkb - 1;
+    f.f_first = kb == 0 || (FOFF > 0 && kr == FOFF);
+    f.f_last = kr == (FOFF + kbpc - 1) % kbpc || kb == nkb - 1;
+    f.f_before_d = FOFF > 0 && f.first_in_chunk && kb != 0;
+    return f;
+}
+
+// The MMA issuer warp and the wait helper warp meet at named barrier 1 (both
+// warps, all lanes); each passes whether it gives up, and both learn whether
+// either did.  Returns true when neither gave up.
+__device__ __forceinline__ bool meet_helper(bool give_up) {
+    uint32_t any;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "barrier.red.or.pred p, 1, 64, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(any)
+        : "r"(give_up ? 1u : 0u)
+        : "memory");
+    return any == 0;
+}
 
 // ---------------------------------------------------------------------------
 // Operand preparation
@@ -1077,52 +1112,45 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0 && rank == 0) {
-            uint32_t it = 0, chunk = 0, fchunk = 0, tcount = 0;
+        // The warp runs the loop together and lane 0 issues.  It waits on no
+        // pipeline barrier itself (a barrier wait in the issuing thread stalls
+        // the MMA stream): the wait helper warp makes those waits and meets this
+        // warp at named barrier 1 once a stage's operands (and the accumulators
+        // it overwrites) are ready, with a flag that ends both loops together
+        // when a wait gave up.
+        if (rank == 0) {
+            uint32_t it = 0, chunk = 0, fchunk = 0;
             bool ok = true;
-            for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
+            // Operand descriptors of stage 0, part 0; the others differ only in
+            // the start-address field (16-byte units, below 2^14 for every
+            // shared-memory address), so each is one add of a constant.
+            const uint64_t desc_a0 = make_desc(smem_base, G::SBO, G::SWZ);
+            const uint64_t desc_b0 = make_desc(smem_base + G::PARTS * SH::X_BYTES, G::SBO, G::SWZ);
+            for (int t = tile0; t < ntiles && ok; t += tstep) {
                 const LeafTile lt = tiles[t];
                 const int nkb = tcp[lt.prod].K_pad / G::KBLK;
-                if constexpr (G::F_FINAL) {
-                    if (!mbar_wait<CG>(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                }
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int kr = kb % kbpc;
-                    const bool first_in_chunk = kr == 0;
-                    const bool last_in_chunk = kr == kbpc - 1 || kb == nkb - 1;
-                    const bool f_first = kb == 0 || (FOFF > 0 && kr == FOFF);
-                    const bool f_last = kr == (FOFF + kbpc - 1) % kbpc || kb == nkb - 1;
+                    const StageFlags fl = stage_flags<kbpc, FOFF>(kb, nkb);
                     const uint32_t buf = chunk % G::DBUF;
-                    const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
-                    if (!mbar_wait<CG>(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA)) {
+                    const uint32_t s = it % NSTAGE;
+                    if (!meet_helper(false)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = smem_base + s * SH::STAGE;
+                    const uint64_t da = desc_a0 + (uint64_t)(s * (SH::STAGE >> 4));
+                    const uint64_t db = desc_b0 + (uint64_t)(s * (SH::STAGE >> 4));
                     auto desc_a = [&](int q, int ks) {
-                        return make_desc(st + q * SH::X_BYTES + ks * G::KSTEP * G::ELEM, G::SBO, G::SWZ);
+                        return da + (uint64_t)((q * SH::X_BYTES + ks * G::KSTEP * G::ELEM) >> 4);
                     };
                     auto desc_b = [&](int q, int ks) {
-                        return make_desc(st + G::PARTS * SH::X_BYTES + q * SH::Y_BYTES + ks * G::KSTEP * G::ELEM,
-                                         G::SBO, G::SWZ);
+                        return db + (uint64_t)((q * SH::Y_BYTES + ks * G::KSTEP * G::ELEM) >> 4);
                     };
-                    // D group of this stage (waits for the drain of the previous D chunk)
-                    auto run_d = [&]() -> bool {
+                    // D group of this stage: order d into accumulator min(d, ND-1);
+                    // each accumulator is overwritten by its first MMA of the chunk
+                    auto run_d = [&]() {
                         if constexpr (G::ND > 0) {
-                            if (first_in_chunk) {
-                                if (!mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
-                                                   ERR_TIMEOUT_MMA))
-                                    return false;
-                                tc_fence_after();
-                            }
-                            // order d into accumulator min(d, ND-1); each accumulator is
-                            // overwritten by its first MMA of the chunk
-                            bool fresh[3] = {first_in_chunk, first_in_chunk, first_in_chunk};
+                            bool fresh[3] = {fl.first_in_chunk, fl.first_in_chunk, fl.first_in_chunk};
 #pragma unroll
                             for (int ord = 0; ord <= G::DMAX; ++ord) {
                                 const int acc = ord < G::ND - 1 ? ord : G::ND - 1;
@@ -1138,18 +1166,13 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                                     }
                                 }
                             }
-                            if (last_in_chunk) umma_commit<CG>(b_dfull + 8 * buf);
+                            if (fl.last_in_chunk) umma_commit<CG>(b_dfull + 8 * buf);
                         }
-                        return true;
                     };
-                    // F group of this stage (waits for the drain of the previous F chunk)
-                    auto run_f = [&]() -> bool {
+                    // F group of this stage
+                    auto run_f = [&]() {
                         if constexpr (HAS_F) {
-                            if (!G::F_FINAL && f_first) {
-                                if (!mbar_wait<CG>(b_fempty, (fchunk & 1) ^ 1, status, ERR_TIMEOUT_MMA)) return false;
-                                tc_fence_after();
-                            }
-                            bool first = G::F_FINAL ? (kb == 0) : f_first;
+                            bool first = G::F_FINAL ? (kb == 0) : fl.f_first;
 #pragma unroll
                             for (int ord = G::FMIN; ord <= G::FMAX; ++ord)
 #pragma unroll
@@ -1162,32 +1185,94 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                                         first = false;
                                     }
                                 }
-                            if (!G::F_FINAL && f_last) umma_commit<CG>(b_ffull);
+                            if (!G::F_FINAL && fl.f_last) umma_commit<CG>(b_ffull);
                         }
-                        return true;
                     };
-                    // While the D accumulators of the previous chunk drain, this
-                    // stage's F MMAs go first and keep the tensor pipe busy.
-                    const bool f_before_d = FOFF > 0 && first_in_chunk && kb != 0;
-                    if (f_before_d ? !(run_f() && run_d()) : !(run_d() && run_f())) {
-                        ok = false;
-                        break;
+                    if (fl.f_before_d) {
+                        // While the D accumulators of the previous chunk drain, this
+                        // stage's F MMAs go first and keep the tensor pipe busy; the
+                        // D MMAs follow once the helper has seen the drain end.
+                        if (lane == 0) run_f();
+                        __syncwarp();
+                        if (!meet_helper(false)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        if (lane == 0) run_d();
+                    } else if (lane == 0) {
+                        run_d();
+                        run_f();
                     }
-                    umma_commit<CG>(b_empty + 8 * s);  // stage reusable once these MMAs finish
-                    if (last_in_chunk) ++chunk;
-                    if (f_last) ++fchunk;
+                    if (lane == 0) umma_commit<CG>(b_empty + 8 * s);  // stage reusable once these MMAs finish
+                    __syncwarp();
+                    if (fl.last_in_chunk) ++chunk;
+                    if (fl.f_last) ++fchunk;
                 }
                 if (!ok) break;
-                if constexpr (G::F_FINAL) umma_commit<CG>(b_ffull);
+                if constexpr (G::F_FINAL) {
+                    if (lane == 0) umma_commit<CG>(b_ffull);
+                    __syncwarp();
+                }
             }
             // every issued MMA completes before TMEM is released (bounded)
-            umma_commit<CG>(b_done);
-            mbar_wait_quiet<CG>(b_done, 0);
+            if (lane == 0) {
+                umma_commit<CG>(b_done);
+                mbar_wait_quiet<CG>(b_done, 0);
+            }
+            __syncwarp();
         } else if (lane == 0) {
             // odd CTA of a pair: the even CTA's final commit arrives here too
             mbar_wait_quiet<CG>(b_done, 0);
         }
-    } else {
+    } else if (warp == 2 + G::EPI_WARPS) {
+        // ------------------------------------------------------------ wait helper
+        // Makes the MMA issuer's barrier waits, stage by stage in the issuer's
+        // order, and meets it at named barrier 1 after each set (an F-first
+        // stage meets it twice: operands ready, then D accumulators drained).
+        if (rank == 0) {
+            uint32_t it = 0, chunk = 0, fchunk = 0, tcount = 0;
+            bool ok = true;
+            for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
+                const LeafTile lt = tiles[t];
+                const int nkb = tcp[lt.prod].K_pad / G::KBLK;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const StageFlags fl = stage_flags<kbpc, FOFF>(kb, nkb);
+                    const uint32_t buf = chunk % G::DBUF;
+                    const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
+                    bool good = true;
+                    if (lane == 0) {
+                        if (G::F_FINAL && kb == 0)
+                            good = mbar_wait<CG>(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA);
+                        good = good && mbar_wait<CG>(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA);
+                        if (!fl.f_before_d) {
+                            if (G::ND > 0 && fl.first_in_chunk)
+                                good = good && mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
+                                                             ERR_TIMEOUT_MMA);
+                            if (HAS_F && !G::F_FINAL && fl.f_first)
+                                good = good && mbar_wait<CG>(b_fempty, (fchunk & 1) ^ 1, status, ERR_TIMEOUT_MMA);
+                        }
+                    }
+                    if (!meet_helper(!__shfl_sync(0xffffffffu, good, 0))) {
+                        ok = false;
+                        break;
+                    }
+                    if (fl.f_before_d) {
+                        good = true;
+                        if (lane == 0)
+                            good = mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
+                                                 ERR_TIMEOUT_MMA);
+                        if (!meet_helper(!__shfl_sync(0xffffffffu, good, 0))) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (fl.last_in_chunk) ++chunk;
+                    if (fl.f_last) ++fchunk;
+                }
+            }
+        }
+    } else if (warp < 2 + G::EPI_WARPS) {
         // ------------------------------------------------------------ epilogue
         // Thread = one row (TMEM lane) of the tile and NCOL of its columns; the
         // running sum of the drained chunks is hi (registers) + lo (smem).

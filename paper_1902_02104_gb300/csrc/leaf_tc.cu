@@ -428,7 +428,7 @@ struct Geo<MODE_BF16X3> {
 
 template <>
 struct Geo<MODE_TF32> {
-    static constexpr int PARTS = 1, ELEM = 4, KBLK = 32, ROWB = 128, KSTEP = 8, NSTAGE = 6, NSTAGE2 = 8;
+    static constexpr int PARTS = 1, ELEM = 4, KBLK = 64, ROWB = 128, KSTEP = 8, NSTAGE = 3, NSTAGE2 = 4;
     static constexpr uint32_t SWZ = 2, SBO = 1024;  // 128B swizzle
     static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0, HEAD = 0;
     static constexpr bool F_FINAL = true, SLICED = false, FP64_SUM = false;
@@ -457,7 +457,14 @@ template <int MODE, int CG>
 struct Shape {
     using G = Geo<MODE>;
     static constexpr int XROWS = 128, YROWS = 128 / CG;
-    static constexpr int X_BYTES = XROWS * G::ROWB, Y_BYTES = YROWS * G::ROWB;
+    // A K block of a part is ATOMS swizzle atoms (ROWB bytes per row each),
+    // stored one after the other; KATOM elements per atom row, KS_ATOM MMA
+    // K steps per atom.
+    static constexpr int ATOMS = G::KBLK * G::ELEM / G::ROWB, KATOM = G::ROWB / G::ELEM;
+    static constexpr int KS_ATOM = G::ROWB / (G::KSTEP * G::ELEM);
+    static constexpr int ATOM_X = XROWS * G::ROWB, ATOM_Y = YROWS * G::ROWB;
+    static constexpr int X_BYTES = ATOMS * ATOM_X, Y_BYTES = ATOMS * ATOM_Y;
+    static_assert(ATOMS >= 1 && ATOMS * G::ROWB == G::KBLK * G::ELEM, "K block of whole swizzle atoms");
     static constexpr int STAGE = G::PARTS * (X_BYTES + Y_BYTES);
     static constexpr int LO = G::ND > 0 ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
     static constexpr int NSTAGE = CG == 1 ? G::NSTAGE : G::NSTAGE2;
@@ -1088,12 +1095,15 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                     if (rank == 0) mbar_expect_tx(b_full + 8 * s, CG * SH::STAGE);
                     const uint32_t st = smem_base + s * SH::STAGE;
 #pragma unroll
-                    for (int q = 0; q < G::PARTS; ++q) {
-                        tma_load_2d<CG>(st + q * SH::X_BYTES, &pr->tmx, b_full_c + 8 * s, kb * G::KBLK,
-                                        q * pr->p_pad + ya);
-                        tma_load_2d<CG>(st + G::PARTS * SH::X_BYTES + q * SH::Y_BYTES, &pr->tmy, b_full_c + 8 * s,
-                                        kb * G::KBLK, q * pr->r_pad + yb);
-                    }
+                    for (int q = 0; q < G::PARTS; ++q)
+#pragma unroll
+                        for (int a = 0; a < SH::ATOMS; ++a) {
+                            const int kx = kb * G::KBLK + a * SH::KATOM;
+                            tma_load_2d<CG>(st + q * SH::X_BYTES + a * SH::ATOM_X, &pr->tmx, b_full_c + 8 * s, kx,
+                                            q * pr->p_pad + ya);
+                            tma_load_2d<CG>(st + G::PARTS * SH::X_BYTES + q * SH::Y_BYTES + a * SH::ATOM_Y, &pr->tmy,
+                                            b_full_c + 8 * s, kx, q * pr->r_pad + yb);
+                        }
                 }
             }
             // copies still in flight land before the CTA may exit (bounded): the
@@ -1140,11 +1150,14 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                     tc_fence_after();
                     const uint64_t da = desc_a0 + (uint64_t)(s * (SH::STAGE >> 4));
                     const uint64_t db = desc_b0 + (uint64_t)(s * (SH::STAGE >> 4));
+                    // MMA K step ks of part q: atom ks / KS_ATOM, offset ks % KS_ATOM in its rows
                     auto desc_a = [&](int q, int ks) {
-                        return da + (uint64_t)((q * SH::X_BYTES + ks * G::KSTEP * G::ELEM) >> 4);
+                        return da + (uint64_t)((q * SH::X_BYTES + (ks / SH::KS_ATOM) * SH::ATOM_X +
+                                                (ks % SH::KS_ATOM) * G::KSTEP * G::ELEM) >> 4);
                     };
                     auto desc_b = [&](int q, int ks) {
-                        return db + (uint64_t)((q * SH::Y_BYTES + ks * G::KSTEP * G::ELEM) >> 4);
+                        return db + (uint64_t)((q * SH::Y_BYTES + (ks / SH::KS_ATOM) * SH::ATOM_Y +
+                                                (ks % SH::KS_ATOM) * G::KSTEP * G::ELEM) >> 4);
                     };
                     // D group of this stage: order d into accumulator min(d, ND-1);
                     // each accumulator is overwritten by its first MMA of the chunk
@@ -1518,7 +1531,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // TMA map of the stacked parts of one operand: rows (parts x rows_pad) of
-// K_pad elements, a box of KBLK x box_rows, swizzled to the UMMA K-major layout.
+// K_pad elements, a box of one swizzle atom (ROWB bytes of K) x box_rows,
+// swizzled to the UMMA K-major layout.
 template <int MODE>
 bool encode_parts(CUtensorMap* map, char* base, int parts, int rows_pad, int K_pad, int box_rows) {
     using G = Geo<MODE>;
@@ -1526,7 +1540,7 @@ bool encode_parts(CUtensorMap* map, char* base, int parts, int rows_pad, int K_p
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)parts * rows_pad};
     const cuuint64_t strides[1] = {(cuuint64_t)K_pad * G::ELEM};
-    const cuuint32_t box[2] = {(cuuint32_t)G::KBLK, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)(G::ROWB / G::ELEM), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt =
         G::ELEM == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;

@@ -422,6 +422,11 @@ struct Geo<MODE_BF16X3> {
     static constexpr int KC = 256, ND = 2, DMAX = 2, DBUF = 2, FMIN = 1, FMAX = 0, HEAD = 0;  // no F group
     static constexpr bool F_FINAL = false, SLICED = true, FP64_SUM = false;
     static constexpr int EPI_WARPS = 16;
+    // single-plan launches: 8 epilogue warps keep both halves of the
+    // float-float sums in registers (64 columns each), leaving the shared
+    // memory to one more stage (batched launches, whose tiles are short,
+    // keep 16 warps)
+    static constexpr bool LO_REGS = true;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 0;
     static constexpr uint32_t IDESC_KIND = (1u << 4) | (1u << 7) | (1u << 10);  // F32 D, bf16 A and B
 };
@@ -433,6 +438,7 @@ struct Geo<MODE_TF32> {
     static constexpr int KC = 1 << 30, ND = 0, DMAX = -1, DBUF = 1, FMIN = 0, FMAX = 0, HEAD = 0;
     static constexpr bool F_FINAL = true, SLICED = false, FP64_SUM = false;
     static constexpr int EPI_WARPS = 8;
+    static constexpr bool LO_REGS = false;
     static constexpr uint32_t TMEM_COLS = 128, F_COL = 0;
     static constexpr uint32_t IDESC_KIND = (1u << 4) | (2u << 7) | (2u << 10);  // F32 D, tf32 A and B
 };
@@ -444,6 +450,7 @@ struct Geo<MODE_OZAKI> {
     static constexpr int KC = 256, ND = 3, DMAX = 2, DBUF = 1, FMIN = 3, FMAX = 5, HEAD = 0;
     static constexpr bool F_FINAL = false, SLICED = true, FP64_SUM = true;
     static constexpr int EPI_WARPS = 16;
+    static constexpr bool LO_REGS = false;
     static constexpr uint32_t TMEM_COLS = 512, F_COL = 384;
     static constexpr uint32_t IDESC_KIND = (1u << 4) | (1u << 7) | (1u << 10);  // F32 D, bf16 A and B
 };
@@ -453,9 +460,11 @@ struct Geo<MODE_OZAKI> {
 // (M = 256, N = 128); each CTA holds 128 rows of the X parts, 64 rows of the
 // Y parts, and the 128 x 128 accumulator rows of its half.  Halving the Y
 // rows each CTA stages halves the B-operand shared-memory reads per MMA.
-template <int MODE, int CG>
+template <int MODE, int CG, int NB = 1>
 struct Shape {
     using G = Geo<MODE>;
+    static constexpr bool LO_REGS = G::LO_REGS && NB == 1;
+    static constexpr int EPI_WARPS = LO_REGS ? 8 : G::EPI_WARPS;
     static constexpr int XROWS = 128, YROWS = 128 / CG;
     // A K block of a part is ATOMS swizzle atoms (ROWB bytes per row each),
     // stored one after the other; KATOM elements per atom row, KS_ATOM MMA
@@ -466,15 +475,15 @@ struct Shape {
     static constexpr int X_BYTES = ATOMS * ATOM_X, Y_BYTES = ATOMS * ATOM_Y;
     static_assert(ATOMS >= 1 && ATOMS * G::ROWB == G::KBLK * G::ELEM, "K block of whole swizzle atoms");
     static constexpr int STAGE = G::PARTS * (X_BYTES + Y_BYTES);
-    static constexpr int LO = G::ND > 0 ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
-    static constexpr int NSTAGE = CG == 1 ? G::NSTAGE : G::NSTAGE2;
+    static constexpr int LO = G::ND > 0 && !LO_REGS ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
+    static constexpr int NSTAGE = (CG == 1 ? G::NSTAGE : G::NSTAGE2) + (LO_REGS ? 1 : 0);
     // CG == 2 keeps at least Y_BYTES of allocation after the last stage, so
     // that the operand reads of its last Y part stay inside this CTA's
     // shared memory whatever the B rows the pair MMA takes per CTA
     static constexpr int TAIL = CG == 2 && LO < Y_BYTES ? Y_BYTES : 0;
     static constexpr int SMEM = NSTAGE * STAGE + LO + 1024 /*align*/ + 256 /*barriers*/ + TAIL;
     static constexpr uint32_t IDESC = G::IDESC_KIND | ((128u >> 3) << 17) | ((128u * CG >> 4) << 24);
-    static constexpr int THREADS = 32 * (3 + G::EPI_WARPS);  // TMA, MMA, epilogue warps, wait helper
+    static constexpr int THREADS = 32 * (3 + EPI_WARPS);  // TMA, MMA, epilogue warps, wait helper
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -1013,13 +1022,13 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
 // even CTA's dempty / fempty barriers count the epilogue warps of both.
 
 template <int NB, int MODE, int CG>
-__global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
+__global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ BindSet<NB> bs, const TcProd* __restrict__ tcp,
                    const LeafTile* __restrict__ tiles, int ntiles, int* __restrict__ status) {
     using G = Geo<MODE>;
-    using SH = Shape<MODE, CG>;
+    using SH = Shape<MODE, CG, NB>;
     constexpr int NSTAGE = SH::NSTAGE;
-    constexpr int NCOL = 128 / (G::EPI_WARPS / 4);  // columns per epilogue thread
+    constexpr int NCOL = 128 / (SH::EPI_WARPS / 4);  // columns per epilogue thread
     constexpr int NG = NCOL / 16;                   // 16-column groups per thread
     constexpr int kbpc = G::KC / G::KBLK > 0 ? G::KC / G::KBLK : 1;
     constexpr bool HAS_F = G::FMIN <= G::FMAX;
@@ -1051,10 +1060,10 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
         }
         for (int s = 0; s < G::DBUF; ++s) {
             mbar_init(b_dfull + 8 * s, 1);
-            mbar_init(b_dempty + 8 * s, G::EPI_WARPS * CG);
+            mbar_init(b_dempty + 8 * s, SH::EPI_WARPS * CG);
         }
         mbar_init(b_ffull, 1);
-        mbar_init(b_fempty, G::EPI_WARPS * CG);
+        mbar_init(b_fempty, SH::EPI_WARPS * CG);
         mbar_init(b_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1238,7 +1247,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
             // odd CTA of a pair: the even CTA's final commit arrives here too
             mbar_wait_quiet<CG>(b_done, 0);
         }
-    } else if (warp == 2 + G::EPI_WARPS) {
+    } else if (warp == 2 + SH::EPI_WARPS) {
         // ------------------------------------------------------------ wait helper
         // Makes the MMA issuer's barrier waits, stage by stage in the issuer's
         // order, and meets it at named barrier 1 after each set (an F-first
@@ -1285,7 +1294,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                 }
             }
         }
-    } else if (warp < 2 + G::EPI_WARPS) {
+    } else if (warp < 2 + SH::EPI_WARPS) {
         // ------------------------------------------------------------ epilogue
         // Thread = one row (TMEM lane) of the tile and NCOL of its columns; the
         // running sum of the drained chunks is hi (registers) + lo (smem).
@@ -1303,6 +1312,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
             float hi[NCOL];
 #pragma unroll
             for (int c = 0; c < NCOL; ++c) hi[c] = 0.f;
+            f32x2 lo2r[SH::LO_REGS ? NCOL / 2 : 1];  // lo halves in registers (LO_REGS)
             if constexpr (G::ND > 0) {
                 // Drains in the order the MMA issuer commits them: stage dnext
                 // ends a D chunk, stage fnext an F chunk (the tile's last stage
@@ -1343,7 +1353,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                                              pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1])), h, l);
                                     if constexpr (G::ND > 2)
                                         l = add2(l, pk2(__uint_as_float(a2[cc]), __uint_as_float(a2[cc + 1])));
-                                    f32x2* lp = lo2_s + ((col + c) / 2) * 128 + row;
+                                    f32x2* lp = SH::LO_REGS ? &lo2r[(g * 16 + c) / 2] : lo2_s + ((col + c) / 2) * 128 + row;
                                     two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]), h, s2, e2);
                                     e2 = add2(e2, add2(lo_init ? *lp : 0ull, l));
                                     const f32x2 hn = add2(s2, e2);  // Fast2Sum: |s2| >= |e2|
@@ -1445,7 +1455,10 @@ __global__ void __launch_bounds__(Shape<MODE, CG>::THREADS, 1)
                             const int j = j0 + g * 16 + c;
                             ok[q] = j < p_out_cols && (dense_out || p_out_kind == OUT_PACKED || (int64_t)p_cj0 + j >= gi);
                             float hh = hi[g * 16 + c],
-                                  ll = G::ND > 0 ? lo_s[(((col + c) / 2) * 128 + row) * 2 + ((col + c) & 1)] : 0.f;
+                                  ll = G::ND == 0 ? 0.f
+                                       : SH::LO_REGS ? (((c & 1) == 0) ? __uint_as_float((uint32_t)lo2r[(g * 16 + c) / 2])
+                                                                      : __uint_as_float((uint32_t)(lo2r[(g * 16 + c) / 2] >> 32)))
+                                                    : lo_s[(((col + c) / 2) * 128 + row) * 2 + ((col + c) & 1)];
                             ff_add(hh, ll, f[c]);
                             if constexpr (!G::FP64_SUM) {
                                 // FP32-accuracy modes: the FP32 sum of the pair, widened
@@ -1614,7 +1627,7 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
             return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, MODE, 2>, bs, t.tcp, t.tiles, t.ntiles, t.status);
         }
     }
-    using SH = Shape<MODE, 1>;
+    using SH = Shape<MODE, 1, NB>;
     const int grid = std::max(1, std::min(t.ntiles, g_sms));
     tc_gemm_kernel<NB, MODE, 1><<<grid, SH::THREADS, SH::SMEM, s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status);
     return cudaGetLastError();
@@ -1633,7 +1646,7 @@ cudaError_t launch_kind(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
 template <int NB, int MODE, int CG>
 cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(tc_gemm_kernel<NB, MODE, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Shape<MODE, CG>::SMEM);
+                                Shape<MODE, CG, NB>::SMEM);
 }
 
 // How many CTA pairs of the MODE kernel fit on the device at once (0 when the

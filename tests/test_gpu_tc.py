@@ -104,11 +104,16 @@ def test_ozaki_wide_exponent_range(gpu):
     assert err <= 1e-11, err
 
 
-def test_tc_batched_equals_single(gpu):
+@pytest.mark.parametrize("dtype", [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI])
+def test_tc_batched_equals_single(gpu, dtype):
+    # batched launches run their own kernel layout (and, for the FP64
+    # emulation, merged column-maxima segments across instances): the same
+    # bits as the single-plan launches
     import torch
     shapes = [(300, 200), (1000, 129), (129, 400), (777, 333)]
-    mats = [inputs.normal(m, n, seed=i, dtype=np.float32) for i, (m, n) in enumerate(shapes)]
-    plans = [ata.Plan(m, n, ata.ATA_F32_BF16X3, 128) for m, n in shapes]
+    f64 = dtype == ata.ATA_F64_OZAKI
+    mats = [inputs.normal(m, n, seed=i, dtype=np.float64 if f64 else np.float32) for i, (m, n) in enumerate(shapes)]
+    plans = [ata.Plan(m, n, dtype, 128) for m, n in shapes]
     dev = [torch.from_numpy(a).cuda() for a in mats]
     singles = [p(d).clone() for p, d in zip(plans, dev)]
     Cs = ata.ata_execute_batched(plans, dev)

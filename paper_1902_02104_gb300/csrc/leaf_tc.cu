@@ -999,6 +999,9 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
 // ---------------------------------------------------------------------------
 // Persistent tcgen05 GEMM over leaf tiles
 //
+// Warps: 0 TMA producer (lane 0), 1 MMA issuer (lane 0 issues, the warp
+// meets the helper), 2 .. 1 + EPI_WARPS epilogue (TMEM drains and stores),
+// 2 + EPI_WARPS wait helper (the issuer's pipeline-barrier waits).
 // CG == 1: one CTA per SM, each CTA takes tiles blockIdx.x, + gridDim.x, ...
 // CG == 2: clusters of two CTAs (a pair on two SMs); each pair takes tiles
 // clusterid, + nclusterid, ...  Both CTAs run the TMA producer for their own

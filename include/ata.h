@@ -153,8 +153,9 @@ typedef struct {
     int32_t cta_pair;            /* tensor-core leaves: 1 = 256 x 128 output
                                     tiles computed by CTA pairs (two SMs,
                                     tcgen05 cta_group::2) when every leaf is
-                                    wider than 128 rows; -1 or 0 = 128 x 128
-                                    tiles on single CTAs (default)           */
+                                    wider than 128 rows; 0 = 128 x 128 tiles
+                                    on single CTAs; -1 = the mode's default
+                                    (pairs for TF32, single CTAs otherwise) */
 } ata_plan_options;
 
 /* Same as ata_plan_create with explicit options (opts may not be NULL).

@@ -50,7 +50,7 @@ def test_pair_matches_single_cta(gpu, dtype):
     A = (inputs.normal(m, n, seed=21) if dtype == ata.ATA_F64_OZAKI
          else inputs.scaled_cols(m, n, seed=21)).astype(in_dtype(dtype))
     C2, plan2 = run(A, dtype, cutoff, cta_pair=1)
-    C1, plan1 = run(A, dtype, cutoff)
+    C1, plan1 = run(A, dtype, cutoff, cta_pair=0)
     assert plan2.info["leaf_tile_rows"] == 256
     assert plan1.info["leaf_tile_rows"] == 128
     # the same dot products in the same K order: identical results

@@ -539,8 +539,9 @@ def _line_common(args, world, metric, value, unit, ms, mode, config):
 
 def run_batched(args, mode):
     """Config 4: 512 independent instances, m log-U[64,4096], n log-U[32,1024],
-    U(-1,1), seed 3; one batched execution (merged task tables, one
-    persistent leaf launch, captured graph) per step."""
+    U(-1,1), seed 3; one execution of a prepared batch (the instances packed
+    back to back in one input and one output buffer; merged task tables, one
+    persistent leaf launch per group of 256, captured graphs) per step."""
     import torch
 
     import oracle
@@ -552,11 +553,17 @@ def run_batched(args, mode):
     dt = np.float64 if mode in ("f64", "ozaki") else np.float32
     mats = [a.astype(dt) for a in inputs.batch(512, seed=3)]
     plans = [ata.Plan(a.shape[0], a.shape[1], MODE_CODES[mode], 0) for a in mats]
-    As = [torch.from_numpy(a).to(dev) for a in mats]
-    Cs = [torch.empty(a.shape[1] * (a.shape[1] + 1) // 2, dtype=torch.float64, device=dev) for a in mats]
+    batch = ata.Batch(plans)
+    # the packed input in pinned host memory, and its device copy
+    hostA = torch.zeros(batch.a_numel, dtype=batch.in_dtype).pin_memory()
+    for v, a in zip(batch.input_views(hostA), mats):
+        v.copy_(torch.from_numpy(a))
+    devA = hostA.to(dev)
+    devC = torch.empty(batch.c_numel, dtype=torch.float64, device=dev)
+    hostC = torch.empty(batch.c_numel, dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
-        ata.ata_execute_batched(plans, As, Cs)
+        batch(devA, devC)
     torch.cuda.synchronize()
     sampler = ClockSampler(gpu_smi_index(torch, dev))
     sampler.start()
@@ -567,7 +574,7 @@ def run_batched(args, mode):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        ata.ata_execute_batched(plans, As, Cs)
+        batch(devA, devC)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -575,14 +582,19 @@ def run_batched(args, mode):
     ms = max_over_ranks(torch, e0.elapsed_time(e1) / args.steps, world)
     eff = sum(effective_flops(a.shape[0], a.shape[1]) for a in mats)
     kind, tol = TOLERANCE[mode]
-    errs = []
-    for i in range(0, 512, 64):  # every 64th instance against the full oracle
-        ref = oracle.ata_packed(mats[i])
-        got = Cs[i].cpu().numpy()
-        if kind == "normwise":
-            errs.append(oracle.normwise_error(got, ref, mats[i].shape[1]))
-        else:
-            errs.append(oracle.componentwise_error(got, ref, oracle.abs_gram_packed(mats[i])))
+
+    def sampled_errors(C):
+        errs = []
+        for i, c in list(enumerate(batch.output_views(C)))[::64]:  # every 64th instance, full oracle
+            ref = oracle.ata_packed(mats[i])
+            got = c.cpu().numpy() if c.is_cuda else c.numpy()
+            if kind == "normwise":
+                errs.append(oracle.normwise_error(got, ref, mats[i].shape[1]))
+            else:
+                errs.append(oracle.componentwise_error(got, ref, oracle.abs_gram_packed(mats[i])))
+        return errs
+
+    errs = sampled_errors(devC)
     mults = sum(p.info["mults"] for p in plans)
     leaf_flops = 2.0 * mults * PAIRS[mode]
     achieved = leaf_flops / (ms / 1e3) / 1e12
@@ -591,57 +603,36 @@ def run_batched(args, mode):
     else:
         peak, peak_src = tensor_peak(mode)
         bound = "tensor"
-    # end to end: every step copies all inputs in from pinned host memory and
-    # all results back.  The instances sit back to back in one host buffer
-    # and one device buffer (one copy each way per step), as a caller packing
-    # its batch would lay them out.
-    # Each instance starts on a 256-byte boundary (the C-ABI wants 8).
-    elem = mats[0].dtype.itemsize
-    pad = 256 // elem
-    a_off = np.cumsum([0] + [-(-a.size // pad) * pad for a in mats])
-    c_off = np.cumsum([0] + [-(-c.numel() // 32) * 32 for c in Cs])
-    tdt = torch.float64 if elem == 8 else torch.float32
-    hostA = torch.empty(int(a_off[-1]), dtype=tdt).pin_memory()
-    for i, a in enumerate(mats):
-        hostA[int(a_off[i]):int(a_off[i]) + a.size] = torch.from_numpy(a.reshape(-1))
-    devA = torch.empty(int(a_off[-1]), dtype=tdt, device=dev)
-    devC = torch.empty(int(c_off[-1]), dtype=torch.float64, device=dev)
-    hostC = torch.empty(int(c_off[-1]), dtype=torch.float64).pin_memory()
-    As_p = [devA[int(a_off[i]):int(a_off[i]) + a.size].view(a.shape) for i, a in enumerate(mats)]
-    Cs_p = [devC[int(c_off[i]):int(c_off[i]) + c.numel()] for i, c in enumerate(Cs)]
 
+    # end to end: every step copies the whole packed input in from pinned
+    # host memory and the whole packed output back
     def e2e_step():
         devA.copy_(hostA, non_blocking=True)
-        ata.ata_execute_batched(plans, As_p, Cs_p)
+        batch(devA, devC)
         hostC.copy_(devC, non_blocking=True)
         torch.cuda.synchronize()
+    devC.zero_()
     e2e_step()
+    e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(e2e_steps):
         e2e_step()
-    t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / max(1, min(args.steps, 3)), world)
+    t_e2e = max_over_ranks(torch, (time.perf_counter() - t0) / e2e_steps, world)
+    errs += sampled_errors(hostC)
     line = _line_common(args, world, "effective TFLOP/s (m*n^2 FMAs) of C = A^t A, 512 batched instances",
                         world * eff / (ms / 1e3) / 1e12, "TFLOP/s", ms, mode,
                         {"workload": f"batched_{mode}", "instances": 512, "m_range": [64, 4096],
                          "n_range": [32, 1024], "generator": "uniform(-1,1) seed 3", "cutoff": "autotuned per shape",
-                         "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (%.0f MB)" % (
-                             sum(a.nbytes for a in mats) / 2**20)})
+                         "parallelism": f"replicas{world}", "calls": "one ata_batch_execute per step",
+                         "l2": "inputs larger than L2 (%.0f MB)" % (sum(a.nbytes for a in mats) / 2**20)})
     line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                         "kernel": "whole batched step (leaf flops / step time)", "flops_per_launch": leaf_flops}
     line["e2e"] = {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s",
-                   "h2d_bytes_per_step": int(hostA.numel() * elem),
+                   "h2d_bytes_per_step": int(hostA.numel() * hostA.element_size()),
                    "d2h_bytes_per_step": int(hostC.numel() * 8)}
-    line["gpu_launches"] = int(args.steps * ata.ata_batched_graph_kernels(plans, As))
-    # the packed-buffer results of the last end-to-end step, sampled as above
-    for i in range(0, 512, 64):
-        ref = oracle.ata_packed(mats[i])
-        got = hostC[int(c_off[i]):int(c_off[i]) + Cs[i].numel()].numpy()
-        if kind == "normwise":
-            errs.append(oracle.normwise_error(got, ref, mats[i].shape[1]))
-        else:
-            errs.append(oracle.componentwise_error(got, ref, oracle.abs_gram_packed(mats[i])))
-    line["error"] = {kind + "_max_of_8": max(errs), "tolerance": tol,
+    line["gpu_launches"] = int(args.steps * batch.graph_kernels())
+    line["error"] = {kind + "_max_of_16": max(errs), "tolerance": tol,
                      "checked": "every 64th instance, device-timed and end-to-end results"}
     line["clocks"] = clocks
     if rank == 0:

@@ -231,6 +231,40 @@ ata_status ata_execute_batched(const ata_plan* plans, int count,
                                const void* const* A, const int64_t* lda,
                                double* const* C_packed, void* stream);
 
+/* A prepared batch: the same execution as ata_execute_batched, with the
+ * plans bound once to one packed layout, so that a call passes two device
+ * pointers.  Instance i reads its A at element offset a_off[i] of the input
+ * buffer (leading dimension lda[i]; elements of the plans' input type) and
+ * writes its packed C at element offset c_off[i] of one FP64 output buffer.
+ * The caller sizes both buffers to cover every instance and keeps the
+ * instances' C ranges disjoint.  The merged task tables are built here and
+ * each group of instances captures its graph on the first execution and
+ * again when A or C moves.  The plans must stay alive: destroying one of
+ * them retires the batch (its executions then fail with ATA_EINVAL).
+ * Errors: ATA_EINVAL (NULL out, count < 0, NULL arrays with count > 0, a
+ * NULL or repeated plan, mixed dtype families, lda[i] < max(n_i, 1), a
+ * negative offset), ATA_ENOMEM, ATA_ECUDA. */
+typedef struct ata_batch_s* ata_batch;
+ata_status ata_batch_create(ata_batch* out, const ata_plan* plans, int count,
+                            const int64_t* lda, const int64_t* a_off,
+                            const int64_t* c_off);
+
+/* Queue one execution of the batch on `stream`: A and C are the device
+ * buffers of the layout above (A aligned to its element size, C to 8 bytes).
+ * Returns once the work is queued.  Errors: ATA_EINVAL (NULL batch, NULL or
+ * misaligned A or C with count > 0, a plan of the batch destroyed),
+ * ATA_ECUDA. */
+ata_status ata_batch_execute(ata_batch batch, const void* A, double* C,
+                             void* stream);
+
+/* Kernel launches one execution of the batch makes (the kernel nodes of its
+ * groups' graphs).  Errors: ATA_EINVAL (NULL argument, not executed yet, a
+ * plan destroyed). */
+ata_status ata_batch_graph_kernels(ata_batch batch, int32_t* kernels);
+
+/* Release the batch (waits for the device first).  The plans stay. */
+void ata_batch_destroy(ata_batch batch);
+
 /* Stage timing.  With enable != 0 the plan's graph also records CUDA events
  * on the execution stream around its stages (the graph is re-captured on the
  * next ata_execute).  ata_plan_stage_times fills ms[4] for the most recent

@@ -19,7 +19,7 @@ __all__ = [
     "ATA_F64", "ATA_F32_BF16X3", "ATA_F32_TF32", "ATA_F64_OZAKI", "ATA_STRASSEN", "ATA_WINOGRAD",
     "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
     "ata_execute_host_async", "ata_plan_wait", "ata_batched_graph_kernels",
-    "ata_execute_batched", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
+    "ata_execute_batched", "Batch", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
     "packed_size", "lib_path",
 ]
 
@@ -94,6 +94,11 @@ def load():
         "ata_execute_batched": ([ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                  ctypes.POINTER(vp), vp], i32),
         "ata_plan_destroy": ([vp], None),
+        "ata_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                              ctypes.POINTER(i64)], i32),
+        "ata_batch_execute": ([vp, vp, dp, vp], i32),
+        "ata_batch_graph_kernels": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
+        "ata_batch_destroy": ([vp], None),
         "ata_execute_static_scratch": ([i64, i64, vp, i64, dp, i32, vp], i32),
         "ata_plan_device_status": ([vp, ctypes.POINTER(ctypes.c_int)], i32),
         "ata_plan_graph_kernels": ([vp, ctypes.POINTER(ctypes.c_int32)], i32),
@@ -376,6 +381,91 @@ def ata_execute_batched(plans, As, Cs=None, stream=None):
     cp = (ctypes.c_void_p * count)(*[C.data_ptr() for C in Cs])
     _check(load().ata_execute_batched(ph, count, ap, ld, cp, _stream_handle(stream)))
     return Cs
+
+
+def _round_up(x: int, q: int) -> int:
+    return -(-x // q) * q
+
+
+class Batch:
+    """A prepared batch (``ata_batch_create``): the plans bound once to one
+    packed input buffer and one packed FP64 output buffer, so that
+    ``batch(A, C)`` (``ata_batch_execute``) marshals two pointers.  Without
+    offsets the instances are laid out back to back, each starting on an
+    ``align_bytes`` boundary, A_i row-major with leading dimension n_i."""
+
+    def __init__(self, plans, a_offsets=None, c_offsets=None, lda=None, align_bytes: int = 256):
+        self.plans = list(plans)  # the plans must outlive the batch
+        count = len(self.plans)
+        self.elem = 8 if count == 0 or self.plans[0].dtype in (ATA_F64, ATA_F64_OZAKI) else 4
+        self.lda = [max(p.n, 1) for p in self.plans] if lda is None else [int(x) for x in lda]
+        a_sizes = [(p.m - 1) * l + p.n if p.m > 0 and p.n > 0 else 0 for p, l in zip(self.plans, self.lda)]
+        c_sizes = [packed_size(p.n) for p in self.plans]
+
+        def layout(sizes, elem):
+            offs, off = [], 0
+            for sz in sizes:
+                offs.append(off)
+                off += _round_up(sz, max(1, align_bytes // elem))
+            return offs
+
+        self.a_offsets = layout(a_sizes, self.elem) if a_offsets is None else [int(x) for x in a_offsets]
+        self.c_offsets = layout(c_sizes, 8) if c_offsets is None else [int(x) for x in c_offsets]
+        if len(self.lda) != count or len(self.a_offsets) != count or len(self.c_offsets) != count:
+            raise ValueError("plans, lda and offsets must have the same length")
+        self.a_numel = max([o + sz for o, sz in zip(self.a_offsets, a_sizes)], default=0)
+        self.c_numel = max([o + sz for o, sz in zip(self.c_offsets, c_sizes)], default=0)
+        ph = (ctypes.c_void_p * max(count, 1))(*[p.handle for p in self.plans])
+        ld = (ctypes.c_int64 * max(count, 1))(*self.lda)
+        ao = (ctypes.c_int64 * max(count, 1))(*self.a_offsets)
+        co = (ctypes.c_int64 * max(count, 1))(*self.c_offsets)
+        h = ctypes.c_void_p()
+        _check(load().ata_batch_create(ctypes.byref(h), ph, count, ld, ao, co))
+        self.handle = h
+
+    @property
+    def in_dtype(self):
+        import torch
+        return torch.float64 if self.elem == 8 else torch.float32
+
+    def input_views(self, A):
+        """Instance i's m_i x n_i view (leading dimension lda[i]) of the packed input A."""
+        return [A.as_strided((p.m, p.n), (l, 1), o) for p, l, o in zip(self.plans, self.lda, self.a_offsets)]
+
+    def output_views(self, C):
+        """Instance i's packed n_i(n_i+1)/2 result inside the packed output C."""
+        return [C[o:o + packed_size(p.n)] for p, o in zip(self.plans, self.c_offsets)]
+
+    def execute(self, A, C=None, stream=None):
+        import torch
+        if not A.is_cuda or A.dtype != self.in_dtype or not A.is_contiguous() or A.numel() < self.a_numel:
+            raise ValueError(f"A must be a contiguous {self.in_dtype} CUDA tensor of >= {self.a_numel} elements")
+        if C is None:
+            C = torch.empty(self.c_numel, dtype=torch.float64, device=A.device)
+        if not C.is_cuda or C.dtype != torch.float64 or not C.is_contiguous() or C.numel() < self.c_numel:
+            raise ValueError(f"C must be a contiguous float64 CUDA tensor of >= {self.c_numel} elements")
+        _check(load().ata_batch_execute(self.handle, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                                        _stream_handle(stream)))
+        return C
+
+    __call__ = execute
+
+    def graph_kernels(self) -> int:
+        """Kernel launches one execution makes (nodes of the captured graphs)."""
+        k = ctypes.c_int32()
+        _check(load().ata_batch_graph_kernels(self.handle, ctypes.byref(k)))
+        return k.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ata_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ata_execute_static_scratch(A, C=None, cutoff: int = 64, stream=None):

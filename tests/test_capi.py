@@ -47,6 +47,10 @@ def test_null_plan_rejected_without_device_work():
     assert lib.ata_plan_graph_kernels(None, None) == ata.ATA_EINVAL
     assert lib.ata_batched_graph_kernels(None, -1, None, None) == ata.ATA_EINVAL
     assert lib.ata_server_kernels(None, None) == ata.ATA_EINVAL
+    assert lib.ata_batch_create(None, None, 0, None, None, None) == ata.ATA_EINVAL
+    assert lib.ata_batch_execute(None, None, None, None) == ata.ATA_EINVAL
+    assert lib.ata_batch_graph_kernels(None, None) == ata.ATA_EINVAL
+    lib.ata_batch_destroy(None)
     assert b"NULL" in lib.ata_last_error_message() or lib.ata_last_error_message() != b""
 
 
@@ -59,3 +63,21 @@ def test_server_argument_checks_without_device():
     t = ctypes.c_uint64()
     assert lib.ata_submit(None, 1, 1, None, 1, None, ctypes.byref(t)) == ata.ATA_EINVAL
     assert lib.ata_poll(None, 1, 0) == ata.ATA_EINVAL
+
+
+def test_prepared_batch_argument_checks_without_device():
+    lib = ata.load()
+    h = ctypes.c_void_p()
+    assert lib.ata_batch_create(ctypes.byref(h), None, -1, None, None, None) == ata.ATA_EINVAL
+    assert lib.ata_batch_create(ctypes.byref(h), None, 2, None, None, None) == ata.ATA_EINVAL  # NULL arrays
+    null_plans = (ctypes.c_void_p * 2)(None, None)
+    z = (ctypes.c_int64 * 2)(1, 1)
+    assert lib.ata_batch_create(ctypes.byref(h), null_plans, 2, z, z, z) == ata.ATA_EINVAL  # NULL plan
+    assert not h.value
+    # an empty batch is valid and queues nothing
+    assert lib.ata_batch_create(ctypes.byref(h), None, 0, None, None, None) == ata.ATA_OK
+    assert h.value
+    assert lib.ata_batch_execute(h, None, None, None) == ata.ATA_OK
+    k = ctypes.c_int32(-1)
+    assert lib.ata_batch_graph_kernels(h, ctypes.byref(k)) == ata.ATA_OK and k.value == 0
+    lib.ata_batch_destroy(h)

@@ -395,26 +395,30 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     small = A_np.nbytes < L2_FLUSH_BYTES
     if not small:
-        # the timed region: K steps queued back to back (A is larger than L2)
+        # the timed region: K steps queued back to back (A is larger than L2),
+        # an event between consecutive steps for the per-step distribution
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         e0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             plan(A, C)
+            evs[k].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
+        step_ms = [a.elapsed_time(b) for a, b in zip([e0] + evs[:-1], evs)]
     else:
         # A fits in L2: every step starts from a cold L2 (a buffer larger than
         # L2 is written before it, outside its events)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        tot = 0.0
+        step_ms = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0.record(stream)
             plan(A, C)
             e1.record(stream)
             torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        ms = tot / args.steps
+            step_ms.append(e0.elapsed_time(e1))
+        ms = sum(step_ms) / args.steps
         del flush
     barrier(world)
     clocks = sampler.stop()
@@ -481,6 +485,7 @@ def run_ours(args):
         "error": {err_kind + "_sampled": err, "tolerance": tol, "samples": cnt, "device_status": dev_status},
         "stages_ms": {"split": statistics.mean(split_ms), "prep": statistics.mean(prep_ms),
                       "leaf": statistics.mean(leaf_ms), "combine": statistics.mean(comb_ms)},
+        "step_ms": step_percentiles(step_ms),
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
                      "kernel": kern, "flops_per_launch": leaf_flops},
@@ -529,6 +534,13 @@ def run_ours(args):
     return 0
 
 
+def step_percentiles(step_ms):
+    """Median, p99 (nearest rank), min and max of this rank's timed steps."""
+    v = sorted(step_ms)
+    p99 = v[min(len(v) - 1, max(0, int(np.ceil(0.99 * len(v))) - 1))]
+    return {"median": statistics.median(v), "p99": p99, "min": v[0], "max": v[-1], "count": len(v)}
+
+
 def _line_common(args, world, metric, value, unit, ms, mode, config):
     return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -572,11 +584,14 @@ def run_batched(args, mode):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         batch(devA, devC)
+        evs[k].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip([e0] + evs[:-1], evs)]
     barrier(world)
     clocks = sampler.stop()
     ms = max_over_ranks(torch, e0.elapsed_time(e1) / args.steps, world)
@@ -631,6 +646,7 @@ def run_batched(args, mode):
     line["e2e"] = {"value": world * eff / t_e2e / 1e12, "unit": "TFLOP/s",
                    "h2d_bytes_per_step": int(hostA.numel() * hostA.element_size()),
                    "d2h_bytes_per_step": int(hostC.numel() * 8)}
+    line["step_ms"] = step_percentiles(step_ms)
     line["gpu_launches"] = int(args.steps * batch.graph_kernels())
     line["error"] = {kind + "_max_of_16": max(errs), "tolerance": tol,
                      "checked": "every 64th instance, device-timed and end-to-end results"}
@@ -781,11 +797,14 @@ def run_gemm(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     stage = {"split": [], "prep": [], "leaf": [], "combine": []}
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         plan(X, Y, C)
+        evs[k].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip([e0] + evs[:-1], evs)]
     barrier(world)
     clocks = sampler.stop()
     ms = max_over_ranks(torch, e0.elapsed_time(e1) / args.steps, world)
@@ -840,6 +859,7 @@ def run_gemm(args):
                          "l2": "inputs larger than L2 (X is %d MB)" % (X_np.nbytes >> 20)})
     line["error"] = {kind: err, "tolerance": tol, "samples": 2000, "device_status": plan.device_status()}
     line["stages_ms"] = {k: statistics.mean(v) for k, v in stage.items()}
+    line["step_ms"] = step_percentiles(step_ms)
     line["roofline"] = {"bound": bound, "achieved": leaf_flops / leaf_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": leaf_flops / leaf_s / 1e12 / peak, "traffic": None, "peak_source": peak_src,
                         "kernel": kern, "flops_per_launch": leaf_flops}

@@ -103,8 +103,10 @@ typedef struct {
     int64_t workspace_bytes;    /* device workspace the plan allocates      */
     int32_t leaf_tile_rows;     /* output tile of the leaf kernel: rows ... */
     int32_t leaf_tile_cols;     /* ... and columns.  Tensor-core leaves use
-                                   256 x 128 tiles (two SMs per tile, a CTA
-                                   pair) when every leaf is padded to them;
+                                   CTA-pair tiles (two SMs per tile; 256 x
+                                   256 for TF32, 256 x 128 otherwise) when
+                                   every leaf is padded to them and they add
+                                   at most 1/8 to the tile area;
                                    ata_plan_query reports the planned shape,
                                    ata_plan_get_info the one that runs on
                                    the plan's device                        */
@@ -150,10 +152,12 @@ typedef struct {
                                     Winograd's variant; 1 for the FP32 modes) */
     int32_t max_strassen_levels; /* cap on Strassen levels per product
                                     (-1 = none; 0 = classical products)        */
-    int32_t cta_pair;            /* tensor-core leaves: 1 = 256 x 128 output
-                                    tiles computed by CTA pairs (two SMs,
-                                    tcgen05 cta_group::2) when every leaf is
-                                    wider than 128 rows; 0 = 128 x 128 tiles
+    int32_t cta_pair;            /* tensor-core leaves: 1 = output tiles
+                                    computed by CTA pairs (two SMs, tcgen05
+                                    cta_group::2; 256 x 256 for TF32, 256 x
+                                    128 otherwise) when every leaf is wider
+                                    than 128 rows and the pair tiles add at
+                                    most 1/8 to the tile area; 0 = 128 x 128 tiles
                                     on single CTAs; -1 = the mode's default
                                     (pairs for TF32, single CTAs otherwise) */
 } ata_plan_options;

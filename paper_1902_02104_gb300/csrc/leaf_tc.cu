@@ -28,7 +28,8 @@
 //
 // Stage 2 (persistent GEMM, one CTA per SM): warp 0 issues TMA loads of all
 // parts of a K-block into a stage ring, warp 1 issues tcgen05.mma (M = 128,
-// N = 128, FP32 accumulators in TMEM), the epilogue warps drain TMEM
+// N = 128, FP32 accumulators in TMEM; CTA pairs M = 256, N = 128, or 256 for
+// TF32), the epilogue warps drain TMEM
 // (tcgen05.ld) and write the FP64 tile.  Every wait on an mbarrier is bounded
 // (1 s, %globaltimer); on timeout the kernel records an error code in the
 // table's status word, the other roles notice it and give up too, in-flight
@@ -436,16 +437,21 @@ struct Geo<MODE_OZAKI> {
 };
 
 // Per-CTA shapes of the leaf GEMM.  CG == 1: one CTA computes a 128 x 128
-// tile (M = N = 128).  CG == 2: a pair of CTAs computes a 256 x 128 tile
-// (M = 256, N = 128); each CTA holds 128 rows of the X parts, 64 rows of the
-// Y parts, and the 128 x 128 accumulator rows of its half.  Halving the Y
+// tile (M = N = 128).  CG == 2: a pair of CTAs computes a 256 x TN tile
+// (M = 256, N = TN); each CTA holds 128 rows of the X parts, TN / 2 rows of
+// the Y parts, and the 128 x TN accumulator rows of its half.  Halving the Y
 // rows each CTA stages halves the B-operand shared-memory reads per MMA.
+// TN = 256 for TF32 (one accumulator, so 256 TMEM columns hold it): twice
+// the MMA work per staged byte, which the 4-byte operands need most; 128
+// for the split modes, whose several accumulators fill TMEM at N = 128.
 template <int MODE, int CG, int NB = 1>
 struct Shape {
     using G = Geo<MODE>;
     static constexpr bool LO_REGS = G::LO_REGS && NB == 1;
     static constexpr int EPI_WARPS = LO_REGS ? 8 : G::EPI_WARPS;
-    static constexpr int XROWS = 128, YROWS = 128 / CG;
+    static constexpr int TN = MODE == MODE_TF32 && CG == 2 ? 256 : 128;
+    static constexpr int XROWS = 128, YROWS = TN / CG;
+    static constexpr uint32_t TMEM_COLS = G::ND == 0 && (uint32_t)TN > G::TMEM_COLS ? (uint32_t)TN : G::TMEM_COLS;
     // A K block of a part is ATOMS swizzle atoms (ROWB bytes per row each),
     // stored one after the other; KATOM elements per atom row, KS_ATOM MMA
     // K steps per atom.
@@ -456,13 +462,13 @@ struct Shape {
     static_assert(ATOMS >= 1 && ATOMS * G::ROWB == G::KBLK * G::ELEM, "K block of whole swizzle atoms");
     static constexpr int STAGE = G::PARTS * (X_BYTES + Y_BYTES);
     static constexpr int LO = G::ND > 0 && !LO_REGS ? 128 * 128 * 4 : 0;  // float-float lo halves, [col][row]
-    static constexpr int NSTAGE = (CG == 1 ? G::NSTAGE : G::NSTAGE2) + (LO_REGS ? 1 : 0);
+    static constexpr int NSTAGE = (CG == 1 || TN > 128 ? G::NSTAGE : G::NSTAGE2) + (LO_REGS ? 1 : 0);
     // CG == 2 keeps at least Y_BYTES of allocation after the last stage, so
     // that the operand reads of its last Y part stay inside this CTA's
     // shared memory whatever the B rows the pair MMA takes per CTA
     static constexpr int TAIL = CG == 2 && LO < Y_BYTES ? Y_BYTES : 0;
     static constexpr int SMEM = NSTAGE * STAGE + LO + 1024 /*align*/ + 256 /*barriers*/ + TAIL;
-    static constexpr uint32_t IDESC = G::IDESC_KIND | ((128u >> 3) << 17) | ((128u * CG >> 4) << 24);
+    static constexpr uint32_t IDESC = G::IDESC_KIND | (((uint32_t)TN >> 3) << 17) | ((128u * CG >> 4) << 24);
     static constexpr int THREADS = 32 * (3 + EPI_WARPS);  // TMA, MMA, epilogue warps, wait helper
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
@@ -1017,7 +1023,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
     using G = Geo<MODE>;
     using SH = Shape<MODE, CG, NB>;
     constexpr int NSTAGE = SH::NSTAGE;
-    constexpr int NCOL = 128 / (SH::EPI_WARPS / 4);  // columns per epilogue thread
+    constexpr int NCOL = SH::TN / (SH::EPI_WARPS / 4);  // columns per epilogue thread
     constexpr int NG = NCOL / 16;                   // 16-column groups per thread
     constexpr int kbpc = G::KC / G::KBLK > 0 ? G::KC / G::KBLK : 1;
     constexpr bool HAS_F = G::FMIN <= G::FMAX;
@@ -1061,7 +1067,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        tmem_alloc<CG>(smem_u32(tmem_slot), G::TMEM_COLS);
+        tmem_alloc<CG>(smem_u32(tmem_slot), SH::TMEM_COLS);
         tmem_relinquish<CG>();
     }
     tc_fence_before();
@@ -1087,7 +1093,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                 const TcProd* pr = tcp + lt.prod;
                 const int nkb = pr->K_pad / G::KBLK;
                 const int ya = lt.ti * (128 * CG) + (int)rank * SH::XROWS;
-                const int yb = lt.tj * 128 + (int)rank * SH::YROWS;
+                const int yb = lt.tj * SH::TN + (int)rank * SH::YROWS;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
                     if (!mbar_wait<CG>(b_empty + 8 * s, ph ^ 1, status, ERR_TIMEOUT_PRODUCER)) {
@@ -1415,7 +1421,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
             const unsigned long long* __restrict__ p_ey = reinterpret_cast<const unsigned long long*>(pr->ey);
             const Bind& bind = bs.b[pr->inst];
             const int i = lt.ti * (128 * CG) + (int)rank * 128 + row;
-            const int j0 = lt.tj * 128 + cq * NCOL;
+            const int j0 = lt.tj * SH::TN + cq * NCOL;
             const bool row_ok = i < p_out_rows;
             int Ei = 0;
             if constexpr (G::SLICED) {
@@ -1515,7 +1521,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
         cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc<CG>(tmem, G::TMEM_COLS);
+        tmem_dealloc<CG>(tmem, SH::TMEM_COLS);
     }
 }
 
@@ -1727,8 +1733,11 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         TcProd& t = tp[i];
         std::memset(&t, 0, sizeof(t));
         char* W = ws[lp.inst];
-        // CTA pairs: each CTA stages 128 X rows and half of the 128 Y rows
-        const int ybox = h.tile_rows == kTcPairRows ? kTcTile / 2 : kTcTile;
+        // CTA pairs: each CTA stages 128 X rows and half of the tile's Y rows
+        // (128 of 256 for TF32, 64 of 128 otherwise); rows past the operand's
+        // padded extent read as zeros (TMA fill) and feed only columns that
+        // are never written
+        const int ybox = h.tile_rows == kTcPairRows ? tc_cols_for(h.leaf, kTcPairRows) / 2 : kTcTile;
         if (!encode_for(h.leaf, &t.tmx, W + lp.tc_x_off, lp.p_pad, lp.K_pad, kTcTile) ||
             !encode_for(h.leaf, &t.tmy, W + lp.tc_y_off, lp.r_pad, lp.K_pad, ybox))
             return fail(ATA_ECUDA, "cuTensorMapEncodeTiled failed for a leaf operand");

@@ -397,13 +397,14 @@ void finish_plan(Plan& P, const Ctx& c, const PlanOptions& opt) {
     P.ws_bytes = c.ws;
     if (P.leaf != LEAF_F64) {
         // CTA-pair tiles when every X operand is padded to them and they add
-        // at most 1/8 to the tile area of 128-row tiles
+        // at most 1/8 to the tile area of 128 x 128 tiles
         bool all = !P.products.empty();
         double a1 = 0, a2 = 0;
+        const int pc = tc_cols_for(P.leaf, kTcPairRows);
         for (const LeafProduct& lp : P.products) {
             all = all && lp.p_pad % kTcPairRows == 0;
             a1 += (double)leaf_tiles(lp, kTcTile, kTcTile) * kTcTile * kTcTile;
-            a2 += (double)leaf_tiles(lp, kTcPairRows, kTcTile) * kTcPairRows * kTcTile;
+            a2 += (double)leaf_tiles(lp, kTcPairRows, pc) * kTcPairRows * pc;
         }
         P.tc_tile_rows = opt.cta_pair && all && a2 <= 1.125 * a1 ? kTcPairRows : kTcTile;
     }

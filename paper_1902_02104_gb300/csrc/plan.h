@@ -130,7 +130,8 @@ struct Plan {
     std::vector<std::vector<CombineTask>> combine_levels; // [l] children at level l+1 -> level l
     int64_t ws_bytes = 0;
     int tc_tile_rows = 0;     // tensor-core leaves: 256 when every X operand is padded to
-                              // whole 256-row tiles (the CTA-pair kernel applies), else 128
+                              // whole 256-row tiles (the CTA-pair kernel applies), else 128;
+                              // the tile's columns are tc_cols_for(leaf, tc_tile_rows)
     PlanStats stats;
 };
 
@@ -142,7 +143,13 @@ struct TcGeom {
 };
 TcGeom tc_geom(LeafKind k);
 constexpr int kTcTile = 128;      // tensor-core leaf tile (rows and columns)
-constexpr int kTcPairRows = 256;  // rows of the CTA-pair tile (columns stay kTcTile)
+constexpr int kTcPairRows = 256;  // rows of the CTA-pair tile
+constexpr int kTcWideCols = 256;  // columns of the TF32 CTA-pair tile
+// Columns of the tensor-core leaf tile with `tile_rows` rows: the TF32 pair
+// kernel computes 256 x 256 tiles (N = 256), every other one 128 columns.
+inline int tc_cols_for(LeafKind k, int tile_rows) {
+    return k == LEAF_TF32 && tile_rows == kTcPairRows ? kTcWideCols : kTcTile;
+}
 
 struct PlanOptions {
     int cutoff = 64;

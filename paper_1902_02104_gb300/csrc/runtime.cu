@@ -146,8 +146,8 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h, int
     }
     for (size_t i = 0; i < P.products.size(); ++i) {
         const LeafProduct& lp = P.products[i];
-        const int tn = leaf_tile(P.leaf);
-        const int tm = P.leaf == LEAF_F64 ? tn : h->tile_rows;
+        const int tm = P.leaf == LEAF_F64 ? kF64Tile : h->tile_rows;
+        const int tn = P.leaf == LEAF_F64 ? kF64Tile : tc_cols_for(P.leaf, tm);
         const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tn - 1) / tn;
         for (int64_t ti = 0; ti < a; ++ti)
             for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti * tm / tn : 0); tj < b; ++tj) {
@@ -210,7 +210,6 @@ void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt) {
     h->comb_pending.clear();
 }
 
-int leaf_tile(LeafKind k) { return k == LEAF_F64 ? kF64Tile : kTcTile; }
 
 void DeviceTables::free_all() {
     if (blob) cudaFree(blob);
@@ -497,7 +496,8 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     out->max_strassen_levels = P.stats.max_strassen_levels;
     out->n_leaf_products = (int32_t)P.products.size();
     int64_t tiles = 0;
-    const int tn = leaf_tile(P.leaf), tm = P.leaf == LEAF_F64 ? tn : P.tc_tile_rows;  // planned tile shape
+    const int tm = P.leaf == LEAF_F64 ? kF64Tile : P.tc_tile_rows;  // planned tile shape
+    const int tn = P.leaf == LEAF_F64 ? kF64Tile : tc_cols_for(P.leaf, tm);
     for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, tm, tn);
     out->n_leaf_tiles = (int32_t)tiles;
     int64_t ns = 0, nc = 0;
@@ -892,11 +892,12 @@ ata_status ata_plan_get_info(ata_plan plan, ata_plan_info* out) {
     if (plan->plan.leaf != LEAF_F64) {
         // the tile shape that runs on this device (the CTA-pair kernel may be
         // unavailable), and the tile count for it
-        const int tm = tc_rows_for(plan->plan);
+        const int tm = tc_rows_for(plan->plan), tn = tc_cols_for(plan->plan.leaf, tm);
         int64_t tiles = 0;
-        for (const LeafProduct& lp : plan->plan.products) tiles += leaf_tiles(lp, tm, kTcTile);
+        for (const LeafProduct& lp : plan->plan.products) tiles += leaf_tiles(lp, tm, tn);
         out->n_leaf_tiles = (int32_t)tiles;
         out->leaf_tile_rows = tm;
+        out->leaf_tile_cols = tn;
     }
     return ATA_OK;
 }

@@ -128,7 +128,6 @@ ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cuda
                           cudaEvent_t before_gemm = nullptr);
 ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d);
 bool leaf_supported(LeafKind k);
-int leaf_tile(LeafKind k);
 // Row tile of the tensor-core kernel that runs plan P on this device.
 int tc_rows_for(const Plan& P);
 

@@ -80,9 +80,9 @@ double model_time(const Plan& P, ata_dtype d) {
         }
     } else {
         leaf = 0;
-        const int tm = P.tc_tile_rows > 0 ? P.tc_tile_rows : kTcTile;
+        const int tm = P.tc_tile_rows > 0 ? P.tc_tile_rows : kTcTile, tn = tc_cols_for(P.leaf, tm);
         for (const LeafProduct& lp : P.products)
-            leaf += (double)leaf_tiles(lp, tm, kTcTile) * tm * kTcTile * lp.K_pad;
+            leaf += (double)leaf_tiles(lp, tm, tn) * tm * tn * lp.K_pad;
     }
     return leaf / r.leaf_fma + (double)P.stats.adds / r.add + 2.0 * (double)P.ws_bytes / r.hbm +
            prep_bytes(P) / (0.5 * r.hbm) + 2e-6 * (double)(P.split_levels.size() + P.combine_levels.size() + 1);

@@ -103,21 +103,22 @@ def _upper_tiles(rows, tm, tn):
 
 @pytest.mark.parametrize("n", [100, 129, 256, 300, 511, 640, 1000, 1023, 1500, 2047])
 def test_leaf_tile_shape_single_syrk_leaf(n):
-    # one diagonal leaf (n <= cutoff): 128-row tiles unless CTA pairs are on
-    # (option 1, or the default -1 for TF32), every X operand is wider than
-    # one tile and 256-row tiles cover at most 1/8 more area
+    # one diagonal leaf (n <= cutoff): 128 x 128 tiles unless CTA pairs are
+    # on (option 1, or the default -1 for TF32), every X operand is wider than
+    # one tile and the pair tiles (256 x 128; 256 x 256 for TF32) cover at
+    # most 1/8 more area
     for dtype in (ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI):
+        pc = 256 if dtype == ata.ATA_F32_TF32 else 128
         t128 = _upper_tiles(n, 128, 128)
-        t256 = _upper_tiles(n, 256, 128)
-        pair = n > 128 and t256 * 256 <= 1.125 * t128 * 128
+        tp = _upper_tiles(n, 256, pc)
+        pair = n > 128 and tp * 256 * pc <= 1.125 * t128 * 128 * 128
         d = q(300, n, 4096, dtype, cta_pair=0)  # single-CTA 128 x 128 tiles
         assert (d["leaf_tile_rows"], d["leaf_tile_cols"], d["n_leaf_tiles"]) == (128, 128, t128)
         for opt in (1, -1):
             i = q(300, n, 4096, dtype, cta_pair=opt)
             on = opt == 1 or dtype == ata.ATA_F32_TF32
-            assert i["leaf_tile_cols"] == 128
-            assert i["leaf_tile_rows"] == (256 if on and pair else 128), (n, t128, t256, opt)
-            assert i["n_leaf_tiles"] == (t256 if on and pair else t128)
+            shape = (256, pc, tp) if on and pair else (128, 128, t128)
+            assert (i["leaf_tile_rows"], i["leaf_tile_cols"], i["n_leaf_tiles"]) == shape, (n, opt, dtype)
     f = q(300, n, 4096, ata.ATA_F64)
     assert (f["leaf_tile_rows"], f["leaf_tile_cols"]) == (64, 64)
     assert f["n_leaf_tiles"] == _upper_tiles(n, 64, 64)

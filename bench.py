@@ -553,7 +553,7 @@ def run_batched(args, mode):
     """Config 4: 512 independent instances, m log-U[64,4096], n log-U[32,1024],
     U(-1,1), seed 3; one execution of a prepared batch (the instances packed
     back to back in one input and one output buffer; merged task tables, one
-    persistent leaf launch per group of 256, captured graphs) per step."""
+    persistent leaf launch, captured graph) per step."""
     import torch
 
     import oracle

@@ -241,9 +241,10 @@ ata_status ata_execute_batched(const ata_plan* plans, int count,
  * buffer (leading dimension lda[i]; elements of the plans' input type) and
  * writes its packed C at element offset c_off[i] of one FP64 output buffer.
  * The caller sizes both buffers to cover every instance and keeps the
- * instances' C ranges disjoint.  The merged task tables are built here and
- * each group of instances captures its graph on the first execution and
- * again when A or C moves.  The plans must stay alive: destroying one of
+ * instances' C ranges disjoint.  The merged task tables are built here; the
+ * batch's graph is captured on the first execution, and when A or C moves
+ * only the instances' bindings (a device array the kernels read) are
+ * uploaded again.  The plans must stay alive: destroying one of
  * them retires the batch (its executions then fail with ATA_EINVAL).
  * Errors: ATA_EINVAL (NULL out, count < 0, NULL arrays with count > 0, a
  * NULL or repeated plan, mixed dtype families, lda[i] < max(n_i, 1), a
@@ -262,7 +263,7 @@ ata_status ata_batch_execute(ata_batch batch, const void* A, double* C,
                              void* stream);
 
 /* Kernel launches one execution of the batch makes (the kernel nodes of its
- * groups' graphs).  Errors: ATA_EINVAL (NULL argument, not executed yet, a
+ * graph).  Errors: ATA_EINVAL (NULL argument, not executed yet, a
  * plan destroyed). */
 ata_status ata_batch_graph_kernels(ata_batch batch, int32_t* kernels);
 
@@ -286,7 +287,7 @@ ata_status ata_plan_stage_times(ata_plan plan, float* ms);
 ata_status ata_plan_graph_kernels(ata_plan plan, int32_t* kernels);
 
 /* The same for ata_execute_batched(plans, count, ..., lda, ...): the kernel
- * nodes of the graphs of all its groups of instances.  Errors: ATA_EINVAL
+ * nodes of its graph.  Errors: ATA_EINVAL
  * (NULL or invalid argument, or the batch has not been executed yet). */
 ata_status ata_batched_graph_kernels(const ata_plan* plans, int count,
                                      const int64_t* lda, int32_t* kernels);

@@ -2,7 +2,8 @@
 // tables of all instances are merged level by level, so the whole batch is
 // one split launch per level, one persistent leaf launch whose tiles (all
 // instances) run heaviest first, and one combine launch per level, captured
-// once as a CUDA graph per group of instances.
+// once as a CUDA graph.  The kernels read the instances' bindings from a
+// device array, so a batch has no limit on its instance count.
 //
 // Two entry points share this machinery: ata_execute_batched takes pointer
 // arrays on every call (tables found by the set of plans), and a prepared
@@ -59,7 +60,7 @@ ata_status check_batch(const ata_plan* plans, int count, const int64_t* lda, Lea
     return ATA_OK;
 }
 
-// Merged tables of instances [g0, g1) (at most kMaxBatchBind of them).
+// Merged tables of instances [g0, g1).
 ata_status build_entry(const ata_plan* plans, const int64_t* lda, int g0, int g1, LeafKind leaf,
                        std::unique_ptr<BatchEntry>* out) {
     std::unique_ptr<BatchEntry> e(new BatchEntry());
@@ -98,13 +99,13 @@ ata_status build_entry(const ata_plan* plans, const int64_t* lda, int g0, int g1
 
 using namespace ata;
 
-// A prepared batch: the plans, their packed layout, and one table set and
-// graph per group of instances.
+// A prepared batch: the plans, their packed layout, and their merged tables
+// and graph.
 struct ata_batch_s {
     std::vector<ata_plan> plans;
     std::vector<int64_t> lda, a_off, c_off;
     std::vector<uint64_t> ids;
-    std::vector<std::unique_ptr<BatchEntry>> groups;
+    std::unique_ptr<BatchEntry> entry;
     std::vector<Bind> binds;  // of the most recent call
     const void* last_A = nullptr;
     double* last_C = nullptr;
@@ -130,7 +131,7 @@ void forget_plan_in_batches(uint64_t id) {
     for (ata_batch_s* b : g_prepared)
         if (!b->dead && std::binary_search(b->ids.begin(), b->ids.end(), id)) {
             b->dead = true;
-            b->groups.clear();  // tables and graphs refer to the plan's workspace
+            b->entry.reset();  // its tables and graph refer to the plan's workspace
         }
 }
 
@@ -155,24 +156,17 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    // groups of at most kMaxBatchBind instances, each one merged table set
-    std::vector<Bind> binds;
-    for (int g0 = 0; g0 < count; g0 += kMaxBatchBind) {
-        const int g1 = std::min(count, g0 + kMaxBatchBind);
-        std::vector<int64_t> gkey(key.begin() + 2 * g0, key.begin() + 2 * g1);
-        auto it = g_batches.find(gkey);
-        if (it == g_batches.end()) {
-            std::unique_ptr<BatchEntry> e;
-            st = build_entry(plans, lda, g0, g1, leaf, &e);
-            if (st != ATA_OK) return st;
-            it = g_batches.emplace(gkey, std::move(e)).first;
-        }
-        binds.clear();
-        for (int i = g0; i < g1; ++i) binds.push_back(make_bind(plans[i], A[i], lda[i], C_packed[i]));
-        st = launch_via_graph(it->second->tables, binds.data(), (int)binds.size(), &it->second->graph, s);
+    auto it = g_batches.find(key);
+    if (it == g_batches.end()) {
+        std::unique_ptr<BatchEntry> e;
+        st = build_entry(plans, lda, 0, count, leaf, &e);
         if (st != ATA_OK) return st;
+        it = g_batches.emplace(key, std::move(e)).first;
     }
-    return ATA_OK;
+    std::vector<Bind> binds;
+    binds.reserve(count);
+    for (int i = 0; i < count; ++i) binds.push_back(make_bind(plans[i], A[i], lda[i], C_packed[i]));
+    return launch_via_graph(it->second->tables, binds.data(), count, &it->second->graph, s);
 }
 
 extern "C" ata_status ata_batched_graph_kernels(const ata_plan* plans, int count, const int64_t* lda,
@@ -186,15 +180,10 @@ extern "C" ata_status ata_batched_graph_kernels(const ata_plan* plans, int count
         key.push_back(lda[i]);
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    int32_t total = 0;
-    for (int g0 = 0; g0 < count; g0 += kMaxBatchBind) {
-        const int g1 = std::min(count, g0 + kMaxBatchBind);
-        auto it = g_batches.find(std::vector<int64_t>(key.begin() + 2 * g0, key.begin() + 2 * g1));
-        if (it == g_batches.end() || !it->second->graph.exec)
-            return fail(ATA_EINVAL, "this batch has not been executed yet");
-        total += it->second->graph.kernels;
-    }
-    *kernels = total;
+    if (count == 0) return ATA_OK;
+    auto it = g_batches.find(key);
+    if (it == g_batches.end() || !it->second->graph.exec) return fail(ATA_EINVAL, "this batch has not been executed yet");
+    *kernels = it->second->graph.kernels;
     return ATA_OK;
 }
 
@@ -220,11 +209,9 @@ extern "C" ata_status ata_batch_create(ata_batch* out, const ata_plan* plans, in
     for (int i = 0; i < count; ++i) b->ids.push_back(plan_id(plans[i]));
     std::sort(b->ids.begin(), b->ids.end());
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    for (int g0 = 0; g0 < count; g0 += kMaxBatchBind) {
-        std::unique_ptr<BatchEntry> e;
-        st = build_entry(plans, lda, g0, std::min(count, g0 + kMaxBatchBind), leaf, &e);
+    if (count > 0) {
+        st = build_entry(plans, lda, 0, count, leaf, &b->entry);
         if (st != ATA_OK) return st;
-        b->groups.push_back(std::move(e));
     }
     g_prepared.insert(b.get());
     *out = b.release();
@@ -249,15 +236,9 @@ extern "C" ata_status ata_batch_execute(ata_batch b, const void* A, double* C, v
         b->last_A = A;
         b->last_C = C;
     }
-    for (size_t g = 0; g < b->groups.size(); ++g) {
-        const int g0 = (int)g * kMaxBatchBind, g1 = std::min(count, g0 + kMaxBatchBind);
-        ata_status st = launch_via_graph(b->groups[g]->tables, b->binds.data() + g0, g1 - g0, &b->groups[g]->graph, s);
-        if (st != ATA_OK) {
-            b->last_A = nullptr;  // rebuild the bindings on the next call
-            return st;
-        }
-    }
-    return ATA_OK;
+    ata_status st = launch_via_graph(b->entry->tables, b->binds.data(), count, &b->entry->graph, s);
+    if (st != ATA_OK) b->last_A = nullptr;  // rebuild the bindings on the next call
+    return st;
 }
 
 extern "C" ata_status ata_batch_graph_kernels(ata_batch b, int32_t* kernels) {
@@ -265,18 +246,15 @@ extern "C" ata_status ata_batch_graph_kernels(ata_batch b, int32_t* kernels) {
     *kernels = 0;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     if (b->dead) return fail(ATA_EINVAL, "a plan of this batch has been destroyed");
-    int32_t total = 0;
-    for (const auto& e : b->groups) {
-        if (!e->graph.exec) return fail(ATA_EINVAL, "this batch has not been executed yet");
-        total += e->graph.kernels;
-    }
-    *kernels = total;
+    if (b->plans.empty()) return ATA_OK;
+    if (!b->entry || !b->entry->graph.exec) return fail(ATA_EINVAL, "this batch has not been executed yet");
+    *kernels = b->entry->graph.kernels;
     return ATA_OK;
 }
 
 extern "C" void ata_batch_destroy(ata_batch b) {
     if (!b) return;
-    if (!b->groups.empty()) cudaDeviceSynchronize();
+    if (b->entry) cudaDeviceSynchronize();
     std::lock_guard<std::mutex> lk(g_batch_mu);
     g_prepared.erase(b);
     delete b;

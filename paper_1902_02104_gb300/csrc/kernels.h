@@ -30,11 +30,20 @@ __host__ __device__ __forceinline__ const T* term_base(const Bind& b, int8_t buf
     return reinterpret_cast<const T*>(buf == BUF_A ? b.A : buf == BUF_B ? b.B : static_cast<const void*>(b.W));
 }
 
-constexpr int kMaxBatchBind = 256;  // instances per batched launch (16 KB of parameters)
+// Bindings of a launch: one instance by value (NB == 1, in the kernel's
+// parameter space), or any number read from a device array (NB == kDevBinds,
+// batched launches; the array is filled before the launch).  Kernels index
+// bs.b[inst] either way.
+constexpr int kDevBinds = 0;
 
 template <int NB>
 struct BindSet {
     Bind b[NB];
+};
+
+template <>
+struct BindSet<kDevBinds> {
+    const Bind* b;
 };
 
 // One output tile of the leaf launch.
@@ -52,8 +61,9 @@ struct Chunk {
 constexpr int kF64Tile = 64;      // FP64 leaf tile (rows and columns)
 constexpr int kMaxTerms = 32;     // terms per operand the leaf kernels accept
 
-// `binds` holds nb <= kMaxBatchBind instances (nb == 1 uses the single-plan
-// instantiation of each kernel).
+// `binds`: nb == 1, the one instance in host memory (passed by value, the
+// single-plan instantiation of each kernel); nb > 1, a device array of nb
+// instances (the kDevBinds instantiation).
 // `status` receives a nonzero code when a self-checked access falls outside its
 // buffer (the access is skipped): 11 leaf read, 12 leaf write, 21 split read,
 // 22 split write, 31 combine read, 32 combine write.

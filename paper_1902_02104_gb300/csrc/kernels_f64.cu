@@ -340,7 +340,10 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Bi
 template <int NB>
 BindSet<NB> make_set(const Bind* binds, int nb) {
     BindSet<NB> s{};
-    for (int i = 0; i < nb && i < NB; ++i) s.b[i] = binds[i];
+    if constexpr (NB == kDevBinds)
+        s.b = binds;  // device array
+    else
+        for (int i = 0; i < nb && i < NB; ++i) s.b[i] = binds[i];
     return s;
 }
 
@@ -352,11 +355,9 @@ cudaError_t launch_leaf_f64(int* status, const Bind* binds, int nb, const LeafPr
     if (nb <= 1)
         leaf_f64_kernel<1><<<grid, NTHREADS, 0, s>>>(make_set<1>(binds, nb), prods, terms, tiles, ntiles, counter,
                                                      status);
-    else if (nb <= kMaxBatchBind)
-        leaf_f64_kernel<kMaxBatchBind><<<grid, NTHREADS, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), prods, terms,
-                                                                 tiles, ntiles, counter, status);
     else
-        return cudaErrorInvalidValue;
+        leaf_f64_kernel<kDevBinds><<<grid, NTHREADS, 0, s>>>(make_set<kDevBinds>(binds, nb), prods, terms, tiles,
+                                                             ntiles, counter, status);
     return cudaGetLastError();
 }
 
@@ -384,10 +385,8 @@ cudaError_t launch_split(int* status, const Bind* binds, int nb, const SplitTask
                          int nchunks, int8_t src_dt, int8_t dst_dt, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
     if (nb <= 1) return split_dispatch<1>(status, make_set<1>(binds, nb), tasks, chunks, nchunks, src_dt, dst_dt, s);
-    if (nb <= kMaxBatchBind)
-        return split_dispatch<kMaxBatchBind>(status, make_set<kMaxBatchBind>(binds, nb), tasks, chunks, nchunks,
-                                             src_dt, dst_dt, s);
-    return cudaErrorInvalidValue;
+    return split_dispatch<kDevBinds>(status, make_set<kDevBinds>(binds, nb), tasks, chunks, nchunks, src_dt, dst_dt,
+                                     s);
 }
 
 cudaError_t launch_combine(int* status, const Bind* binds, int nb, const CombineTask* tasks, const Chunk* chunks,
@@ -395,11 +394,8 @@ cudaError_t launch_combine(int* status, const Bind* binds, int nb, const Combine
     if (nchunks <= 0) return cudaSuccess;
     if (nb <= 1)
         combine_kernel<1><<<nchunks, 256, 0, s>>>(make_set<1>(binds, nb), tasks, chunks, status);
-    else if (nb <= kMaxBatchBind)
-        combine_kernel<kMaxBatchBind><<<nchunks, 256, 0, s>>>(make_set<kMaxBatchBind>(binds, nb), tasks, chunks,
-                                                              status);
     else
-        return cudaErrorInvalidValue;
+        combine_kernel<kDevBinds><<<nchunks, 256, 0, s>>>(make_set<kDevBinds>(binds, nb), tasks, chunks, status);
     return cudaGetLastError();
 }
 

@@ -1685,9 +1685,9 @@ ata_status tc_prepare_device() {
         err = set_smem_attr<1, MODE_BF16X3, 1>();
         if (err == cudaSuccess) err = set_smem_attr<1, MODE_TF32, 1>();
         if (err == cudaSuccess) err = set_smem_attr<1, MODE_OZAKI, 1>();
-        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_BF16X3, 1>();
-        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_TF32, 1>();
-        if (err == cudaSuccess) err = set_smem_attr<kMaxBatchBind, MODE_OZAKI, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<kDevBinds, MODE_BF16X3, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<kDevBinds, MODE_TF32, 1>();
+        if (err == cudaSuccess) err = set_smem_attr<kDevBinds, MODE_OZAKI, 1>();
         if (err == cudaSuccess && !get_encode()) err = cudaErrorNotSupported;
         if (err == cudaSuccess) {
             int dev = 0;
@@ -1983,12 +1983,10 @@ ata_status launch_leaf_tc(const DeviceTables& t, const Bind* binds, int nb, cuda
         BindSet<1> bs{};
         bs.b[0] = binds[0];
         e = launch_kind<1>(t, bs, s, before_gemm);
-    } else if (nb <= kMaxBatchBind) {
-        BindSet<kMaxBatchBind> bs{};
-        for (int i = 0; i < nb; ++i) bs.b[i] = binds[i];
-        e = launch_kind<kMaxBatchBind>(t, bs, s, before_gemm);
     } else {
-        return fail(ATA_EINVAL, "too many instances in one launch");
+        BindSet<kDevBinds> bs{};
+        bs.b = binds;  // device array
+        e = launch_kind<kDevBinds>(t, bs, s, before_gemm);
     }
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core leaf launch");
     return ATA_OK;

@@ -339,6 +339,16 @@ void GraphCache::release() {
     for (int i = 0; i < 5; ++i) ev[i] = nullptr;
     exec = nullptr;
     cap_stream = nullptr;
+    if (launched) cudaEventSynchronize(launched);
+    if (dev_binds) cudaFree(dev_binds);
+    if (stage_binds) cudaFreeHost(stage_binds);
+    for (cudaEvent_t* e : {&uploaded, &launched}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
+    dev_binds = nullptr;
+    stage_binds = nullptr;
+    dev_count = 0;
     binds.clear();
     kernels = 0;
     timed_run = false;
@@ -355,12 +365,44 @@ bool same_binds(const std::vector<Bind>& a, const Bind* b, int nb) {
 // Launches the tables through the cached graph (captured on first use or
 // when the bindings change).
 ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, GraphCache* g, cudaStream_t s) {
-    if (!g->exec || !same_binds(g->binds, binds, nb)) {
-        ata_status st = capture_graph(t, binds, nb, g);
+    if (nb <= 1) {
+        if (!g->exec || !same_binds(g->binds, binds, nb)) {
+            ata_status st = capture_graph(t, binds, nb, g);
+            if (st != ATA_OK) return st;
+            g->binds.assign(binds, binds + nb);
+        }
+        ATA_CUDA(cudaGraphLaunch(g->exec, s));
+        g->timed_run = g->timing;
+        return ATA_OK;
+    }
+    // Several instances: the kernels read the bindings from a device array
+    // that the graph refers to, so buffers that move need an upload of the
+    // array, not a new capture.
+    const size_t bytes = (size_t)nb * sizeof(Bind);
+    if (!g->exec || g->dev_count != nb) {
+        if (g->exec || g->dev_binds) g->release();
+        ATA_CUDA(cudaMalloc(&g->dev_binds, bytes));
+        ATA_CUDA(cudaMallocHost(&g->stage_binds, bytes));
+        ATA_CUDA(cudaEventCreateWithFlags(&g->uploaded, cudaEventDisableTiming));
+        ATA_CUDA(cudaEventCreateWithFlags(&g->launched, cudaEventDisableTiming));
+        g->dev_count = nb;
+        std::memcpy(g->stage_binds, binds, bytes);
+        ATA_CUDA(cudaMemcpy(g->dev_binds, g->stage_binds, bytes, cudaMemcpyHostToDevice));
+        ata_status st = capture_graph(t, g->dev_binds, nb, g);
         if (st != ATA_OK) return st;
+        g->binds.assign(binds, binds + nb);
+    } else if (!same_binds(g->binds, binds, nb)) {
+        // after every earlier launch of the graph (on any stream), and once
+        // the previous upload has left the staging buffer
+        ATA_CUDA(cudaStreamWaitEvent(s, g->launched, 0));
+        ATA_CUDA(cudaEventSynchronize(g->uploaded));
+        std::memcpy(g->stage_binds, binds, bytes);
+        ATA_CUDA(cudaMemcpyAsync(g->dev_binds, g->stage_binds, bytes, cudaMemcpyHostToDevice, s));
+        ATA_CUDA(cudaEventRecord(g->uploaded, s));
         g->binds.assign(binds, binds + nb);
     }
     ATA_CUDA(cudaGraphLaunch(g->exec, s));
+    ATA_CUDA(cudaEventRecord(g->launched, s));
     g->timed_run = g->timing;
     return ATA_OK;
 }

@@ -107,6 +107,14 @@ struct GraphCache {
     bool timing = false;        // graph records ev[] around its stages
     bool timed_run = false;     // an execution with timing has been queued
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // batched graphs (more than one instance): the device array of bindings
+    // the kernels read, its pinned staging buffer, and events that order an
+    // upload after the graph's earlier launches and before the staging
+    // buffer's next refill
+    Bind* dev_binds = nullptr;
+    Bind* stage_binds = nullptr;
+    int dev_count = 0;
+    cudaEvent_t uploaded = nullptr, launched = nullptr;
     void release();
 };
 

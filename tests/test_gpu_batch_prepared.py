@@ -55,8 +55,9 @@ def test_prepared_batch_equals_list_api(gpu, dtype):
             assert oracle.normwise_error(got, want, a.shape[1]) <= tol
 
 
-def test_prepared_batch_two_groups(gpu):
-    # more instances than one launch binds: two table sets, two graphs
+def test_prepared_batch_many_instances(gpu):
+    # more instances (300) than kernel parameters could hold: one launch
+    # sequence reading the bindings from a device array
     import torch
     rng = np.random.default_rng(7)
     shapes = [(int(rng.integers(1, 200)), int(rng.integers(1, 150))) for _ in range(300)]
@@ -151,3 +152,22 @@ def test_prepared_batch_rejects_bad_arguments(gpu):
         batch(torch.zeros(10, dtype=torch.float64, device="cuda"))  # too small
     with pytest.raises(ValueError):
         batch(torch.zeros(batch.a_numel, dtype=torch.float32, device="cuda"))  # wrong dtype
+
+
+def test_list_api_follows_new_pointers(gpu):
+    # ata_execute_batched with the same plans on other tensors: the graph is
+    # kept and the bindings array is uploaded again before the next launch
+    import torch
+    shapes = [(150, 70), (260, 129), (64, 64)]
+    plans = [ata.Plan(m, n, ata.ATA_F32_BF16X3, 64) for m, n in shapes]
+    sets = []
+    for seed in (50, 60, 70):
+        mats = [inputs.integers(m, n, seed=seed + i).astype(np.float32) for i, (m, n) in enumerate(shapes)]
+        dev = [torch.from_numpy(a).cuda() for a in mats]
+        sets.append((mats, dev, ata.ata_execute_batched(plans, dev)))
+    kernels = ata.ata_batched_graph_kernels(plans, sets[0][1])
+    torch.cuda.synchronize()
+    for mats, _, Cs in sets:
+        for a, c in zip(mats, Cs):
+            assert np.array_equal(c.cpu().numpy(), oracle.ata_packed(a))
+    assert kernels == ata.ata_batched_graph_kernels(plans, sets[2][1]) > 0

@@ -102,9 +102,9 @@ def tensor_peak(mode):
 # (profiles/), valid only for the kernel source it was taken on (the first 16
 # hex digits of the sha256 of leaf_tc.cu or kernels_f64.cu).
 LEAF_TRAFFIC = {
-    ("ata_ozaki_10000x10000", "3adcd45656c92553"): 11.139e9 + 0.570e9,
-    ("ata_bf16x3_16384x8192", "3adcd45656c92553"): 6.417e9 + 0.269e9,
-    ("ata_tf32_16384x8192", "3adcd45656c92553"): 2.411e9 + 0.245e9,
+    ("ata_ozaki_10000x10000", "e3737c832598ccb7"): 10.945e9 + 0.571e9,
+    ("ata_bf16x3_16384x8192", "e3737c832598ccb7"): 5.973e9 + 0.270e9,
+    ("ata_tf32_16384x8192", "e3737c832598ccb7"): 2.412e9 + 0.245e9,
     ("ata_f64_10000x10000", "beaf79f07d6f1ff4"): 35.899e9 + 4.653e9,
 }
 

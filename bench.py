@@ -550,7 +550,7 @@ def _line_common(args, world, metric, value, unit, ms, mode, config):
 
 
 def run_batched(args, mode):
-    """Config 4: 512 independent instances, m log-U[64,4096], n log-U[32,1024],
+    """Batched workload: 512 independent instances, m log-U[64,4096], n log-U[32,1024],
     U(-1,1), seed 3; one execution of a prepared batch (the instances packed
     back to back in one input and one output buffer; merged task tables, one
     persistent leaf launch, captured graph) per step."""
@@ -657,7 +657,7 @@ def run_batched(args, mode):
 
 
 def run_serving(args, mode):
-    """Config 5: Poisson arrivals at --rate for --duration seconds; requests
+    """Serving workload: Poisson arrivals at --rate for --duration seconds; requests
     draw matrices from a 256-entry pool (m log-U[128,8192], n log-U[64,2048],
     N(0,1)); admission by a 40 GB budget; plans resident after warm-up."""
     import torch

@@ -29,7 +29,7 @@ def err_c(A_np, C):
     return oracle.componentwise_error(C, oracle.ata_packed(A_np), oracle.abs_gram_packed(A_np))
 
 
-def test_config1_512x384(gpu):
+def test_uniform_512x384_cutoff64(gpu):
     A = inputs.uniform(512, 384, seed=0)
     C, plan = run(A, 64)
     assert plan.info["max_strassen_levels"] == 2

@@ -12,7 +12,7 @@ def q(m, n, cutoff, dtype=ata.ATA_F64, **kw):
     return ata.ata_plan_query(m, n, dtype, cutoff, **kw)
 
 
-def test_config1_tree():
+def test_tree_512x384_cutoff64():
     # 512 x 384, cutoff 64: 512x384 -> 256x192 -> 128x96 -> 64x48 (Eq. "submatrices")
     i = q(512, 384, 64)
     assert i["depth"] == 3

@@ -19,7 +19,7 @@ __all__ = [
     "ATA_F64", "ATA_F32_BF16X3", "ATA_F32_TF32", "ATA_F64_OZAKI", "ATA_STRASSEN", "ATA_WINOGRAD",
     "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
     "ata_execute_host_async", "ata_plan_wait", "ata_batched_graph_kernels",
-    "ata_execute_batched", "Batch", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
+    "ata_execute_batched", "Batch", "packed_layout", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
     "packed_size", "lib_path",
 ]
 
@@ -387,6 +387,30 @@ def _round_up(x: int, q: int) -> int:
     return -(-x // q) * q
 
 
+def packed_layout(shapes, lda=None, elem: int = 8, align_bytes: int = 256):
+    """Back-to-back layout of a batch's instances (m_i, n_i): element offsets
+    of each A_i (row-major, leading dimension lda[i], default n_i) in one
+    input buffer of `elem`-byte elements and of each packed C_i in one FP64
+    output buffer, every instance starting on an `align_bytes` boundary.
+    Returns (lda, a_offsets, c_offsets, a_numel, c_numel)."""
+    shapes = [(int(m), int(n)) for m, n in shapes]
+    lda = [max(n, 1) for _, n in shapes] if lda is None else [int(x) for x in lda]
+    a_sizes = [(m - 1) * l + n if m > 0 and n > 0 else 0 for (m, n), l in zip(shapes, lda)]
+    c_sizes = [packed_size(n) for _, n in shapes]
+
+    def offsets(sizes, e):
+        offs, off = [], 0
+        for sz in sizes:
+            offs.append(off)
+            off += _round_up(sz, max(1, align_bytes // e))
+        return offs
+
+    a_off, c_off = offsets(a_sizes, elem), offsets(c_sizes, 8)
+    a_numel = max([o + sz for o, sz in zip(a_off, a_sizes)], default=0)
+    c_numel = max([o + sz for o, sz in zip(c_off, c_sizes)], default=0)
+    return lda, a_off, c_off, a_numel, c_numel
+
+
 class Batch:
     """A prepared batch (``ata_batch_create``): the plans bound once to one
     packed input buffer and one packed FP64 output buffer, so that
@@ -398,23 +422,15 @@ class Batch:
         self.plans = list(plans)  # the plans must outlive the batch
         count = len(self.plans)
         self.elem = 8 if count == 0 or self.plans[0].dtype in (ATA_F64, ATA_F64_OZAKI) else 4
-        self.lda = [max(p.n, 1) for p in self.plans] if lda is None else [int(x) for x in lda]
-        a_sizes = [(p.m - 1) * l + p.n if p.m > 0 and p.n > 0 else 0 for p, l in zip(self.plans, self.lda)]
-        c_sizes = [packed_size(p.n) for p in self.plans]
-
-        def layout(sizes, elem):
-            offs, off = [], 0
-            for sz in sizes:
-                offs.append(off)
-                off += _round_up(sz, max(1, align_bytes // elem))
-            return offs
-
-        self.a_offsets = layout(a_sizes, self.elem) if a_offsets is None else [int(x) for x in a_offsets]
-        self.c_offsets = layout(c_sizes, 8) if c_offsets is None else [int(x) for x in c_offsets]
+        shapes = [(p.m, p.n) for p in self.plans]
+        self.lda, a_off, c_off, _, _ = packed_layout(shapes, lda, self.elem, align_bytes)
+        self.a_offsets = a_off if a_offsets is None else [int(x) for x in a_offsets]
+        self.c_offsets = c_off if c_offsets is None else [int(x) for x in c_offsets]
         if len(self.lda) != count or len(self.a_offsets) != count or len(self.c_offsets) != count:
             raise ValueError("plans, lda and offsets must have the same length")
+        a_sizes = [(m - 1) * l + n if m > 0 and n > 0 else 0 for (m, n), l in zip(shapes, self.lda)]
         self.a_numel = max([o + sz for o, sz in zip(self.a_offsets, a_sizes)], default=0)
-        self.c_numel = max([o + sz for o, sz in zip(self.c_offsets, c_sizes)], default=0)
+        self.c_numel = max([o + packed_size(n) for o, (_, n) in zip(self.c_offsets, shapes)], default=0)
         ph = (ctypes.c_void_p * max(count, 1))(*[p.handle for p in self.plans])
         ld = (ctypes.c_int64 * max(count, 1))(*self.lda)
         ao = (ctypes.c_int64 * max(count, 1))(*self.a_offsets)

@@ -160,3 +160,21 @@ def test_gemm_invalid_arguments():
         assert e.value.status == ata.ATA_EINVAL
     with pytest.raises(ata.AtaError):
         ata.ata_gemm_query(10, 10, 10, ata.ATA_F64, 8)
+
+
+@pytest.mark.parametrize("p,r", [(1024, 1100), (1000, 1030), (600, 300), (2048, 640), (300, 5000), (129, 129)])
+def test_gemm_pair_tile_shape_follows_area_rule(p, r):
+    # one classical general product (no Strassen level): pair tiles (256 x 256
+    # for TF32, 256 x 128 otherwise) when X is wider than one 128-row tile and
+    # the pair tiles add at most 1/8 to the area of 128 x 128 tiles
+    m = 500
+    for dtype in (ata.ATA_F32_TF32, ata.ATA_F32_BF16X3, ata.ATA_F64_OZAKI):
+        pc = 256 if dtype == ata.ATA_F32_TF32 else 128
+        t128 = -(-p // 128) * -(-r // 128)
+        tp = -(-p // 256) * -(-r // pc)
+        pair = p > 128 and tp * 256 * pc <= 1.125 * t128 * 128 * 128
+        i = ata.ata_gemm_query(m, p, r, dtype, 4096, cta_pair=1)
+        shape = (256, pc, tp) if pair else (128, 128, t128)
+        assert (i["leaf_tile_rows"], i["leaf_tile_cols"], i["n_leaf_tiles"]) == shape, (p, r, dtype)
+        i0 = ata.ata_gemm_query(m, p, r, dtype, 4096, cta_pair=0)
+        assert (i0["leaf_tile_rows"], i0["leaf_tile_cols"], i0["n_leaf_tiles"]) == (128, 128, t128)

@@ -750,6 +750,18 @@ ata_status check_plan_tables(const Plan& P) {
                 (lp.tc_y_off + (int64_t)g.parts * lp.r_pad * lp.K_pad * g.elem) > ws ||
                 lp.K_pad % 64 || lp.p_pad % kTcTile || lp.r_pad % kTcTile || lp.K_pad < lp.K)
                 return fail(ATA_EINVAL, "tensor-core part buffers outside the workspace");
+            // the planned tile grid: a tile stages X rows [ti tm, (ti + 1) tm) and Y
+            // rows [tj tn, (tj + 1) tn) of every part.  X rows stay inside the
+            // padded parts; Y rows may pass the padding only where the operand
+            // has one part (nothing follows it in the tensor map, and the TMA
+            // box reads zeros there) and by at most the odd CTA's half of a tile
+            const int tm = P.tc_tile_rows > 0 ? P.tc_tile_rows : kTcTile, tn = tc_cols_for(P.leaf, tm);
+            const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tn - 1) / tn;
+            if (tm == kTcPairRows && lp.p_pad % kTcPairRows)
+                return fail(ATA_EINVAL, "CTA-pair tiles need X parts padded to whole 256-row tiles");
+            if (a * tm > lp.p_pad) return fail(ATA_EINVAL, "leaf tiles read X rows past the padded parts");
+            if (b * tn > lp.r_pad && !(g.parts == 1 && b * tn - lp.r_pad <= tn / 2))
+                return fail(ATA_EINVAL, "leaf tiles read Y rows past the padded parts");
         }
     }
     for (auto& lv : P.split_levels)

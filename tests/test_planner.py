@@ -178,3 +178,15 @@ def test_gemm_pair_tile_shape_follows_area_rule(p, r):
         assert (i["leaf_tile_rows"], i["leaf_tile_cols"], i["n_leaf_tiles"]) == shape, (p, r, dtype)
         i0 = ata.ata_gemm_query(m, p, r, dtype, 4096, cta_pair=0)
         assert (i0["leaf_tile_rows"], i0["leaf_tile_cols"], i0["n_leaf_tiles"]) == (128, 128, t128)
+
+
+@pytest.mark.parametrize("dtype", [ata.ATA_F32_TF32, ata.ATA_F32_BF16X3, ata.ATA_F64_OZAKI])
+@pytest.mark.parametrize("pair", [0, 1])
+def test_plan_check_tile_grid(dtype, pair):
+    # the host checker walks every product's tile grid for the planned tile
+    # shape: X parts padded to whole tiles, Y rows past the padding only for
+    # one-part operands (TF32's 256-column pair tiles) and by at most half a tile
+    for m, n, c in [(300, 129, 256), (1000, 700, 512), (4097, 1537, 1024), (1000, 3000, 4096), (300, 2048, 512)]:
+        ata.ata_plan_check(m, n, dtype, c, cta_pair=pair)
+    for m, p, r in [(500, 1024, 1100), (500, 1000, 1030), (2000, 600, 300), (500, 2000, 2500), (500, 129, 100)]:
+        ata.ata_gemm_plan_check(m, p, r, dtype, 512, cta_pair=pair)

@@ -320,7 +320,24 @@ def cpu_oracle_sample(A, budget_s=15.0):
             "frac": done / total, "fixed_s": t_fixed}
 
 
+def workload_config(name, world, a_bytes, cutoff):
+    """The config object of an A^t A workload's line (both arms)."""
+    m, n, mode, gen, seed, _ = WORKLOADS[name]
+    small = a_bytes < L2_FLUSH_BYTES
+    return {"workload": name, "m": m, "n": n, "leaf": mode, "generator": f"{gen}(seed={seed})",
+            "cutoff": cutoff if cutoff else "autotuned", "parallelism": f"replicas{world}",
+            "l2": ("L2 flushed before every timed step (A is %.1f MB)" % (a_bytes / 2**20)) if small
+                  else "inputs larger than L2 (A is %d MB)" % (a_bytes >> 20)}
+
+
 def run_reference(args):
+    """The oracle (plain FP64 triple loop, OpenMP over the host cores) on the
+    workload's input.  Every step is one call of the oracle's row routine on
+    a bounded sample of the packed triangle (about --cpu-budget-per-step
+    seconds; successive steps take successive rows), timed whole: ms_per_step
+    is the wall time of the calls that ran, and value their effective rate
+    (the sample's share of the 2 m n^2 effective FLOP over that time)."""
+    import oracle
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
@@ -328,29 +345,49 @@ def run_reference(args):
     m, n, mode, gen, seed, cutoff = WORKLOADS[name]
     A = make_input(name)
     eff = effective_flops(m, n)
-    # each step: a bounded sample (~budget seconds) of the oracle
+    total = m * n * (n + 1) / 2
     budget = max(2.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_oracle_sample(A, budget_s=budget / 4)
-    ts = []
-    samples = []
+
+    def rows_for(r0, seconds, rate):
+        r1, acc = r0, 0.0
+        while r1 < n and acc < rate * seconds:
+            acc += m * (n - r1)
+            r1 += 1
+        return max(r1, r0 + 1)
+
+    # calibration (one of the warm-up calls): multiply-adds per second
+    t0 = time.perf_counter()
+    oracle.ata_rows(A, 0, min(n, 64))
+    rate = m * sum(n - i for i in range(min(n, 64))) / max(time.perf_counter() - t0, 1e-6)
+    r0 = min(n, 64)
+    for _ in range(args.warmup - 1):
+        r1 = rows_for(r0, budget / 4, rate)
+        oracle.ata_rows(A, r0 % n, min(n, r0 % n + (r1 - r0)))
+        r0 = r1 % n
+    times, done = [], []
     for _ in range(args.steps):
-        r = cpu_oracle_sample(A, budget_s=budget)
-        ts.append(r["t_full_s"])
-        samples.append(r)
-    t = statistics.median(ts)
-    value = eff / t / 1e12
-    last = samples[-1]
+        a0 = r0 % n
+        a1 = min(n, rows_for(a0, budget, rate))
+        t0 = time.perf_counter()
+        oracle.ata_rows(A, a0, a1)
+        dt = time.perf_counter() - t0
+        times.append(dt)
+        done.append(m * sum(n - i for i in range(a0, a1)))
+        rate = done[-1] / max(dt, 1e-6)
+        r0 = a1
+    wall = sum(times)
+    frac = sum(done) / args.steps / total
+    value = sum(d / total * eff for d in done) / wall / 1e12
     line = {
         "impl": "reference", "metric": "effective TFLOP/s (m*n^2 FMAs) of C = A^t A", "value": value,
         "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "m": m, "n": n, "generator": f"{gen}(seed={seed})"},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": last["cores"], "kind": "oracle",
-                         "sample": f"packed rows {last['rows'][0]}..{last['rows'][1]} "
-                                   f"({100 * last['frac']:.2f}% of the multiplications) per step, "
-                                   f"extrapolated to the whole product"},
+        "config": workload_config(name, 1, A.nbytes, cutoff),
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: consecutive packed rows ({100 * frac:.2f}% of the product's "
+                                   f"multiplications on average), timed whole; value = the rows' share of "
+                                   f"2 m n^2 over their time"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -477,11 +514,9 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "ozaki": "bf16 (FP64 emulation, 6 slices)", "bf16x3": "bf16 (3 slices)",
                   "tf32": "tf32"}[mode], "data": "synthetic",
-        "config": {"workload": name, "m": m, "n": n, "leaf": mode, "generator": f"{gen}(seed={seed})",
-                   "cutoff": info["cutoff"],
-                   "strassen_levels_max": info["max_strassen_levels"], "parallelism": f"replicas{world}",
-                   "l2": ("L2 flushed before every timed step (A is %.1f MB)" % (A_np.nbytes / 2**20)) if small
-                         else "inputs larger than L2 (A is %d MB)" % (A_np.nbytes >> 20)},
+        "config": workload_config(name, world, A_np.nbytes, cutoff),
+        "plan": {"cutoff": info["cutoff"], "strassen_levels_max": info["max_strassen_levels"],
+                 "leaf_tile": [info["leaf_tile_rows"], info["leaf_tile_cols"]]},
         "error": {err_kind + "_sampled": err, "tolerance": tol, "samples": cnt, "device_status": dev_status},
         "stages_ms": {"split": statistics.mean(split_ms), "prep": statistics.mean(prep_ms),
                       "leaf": statistics.mean(leaf_ms), "combine": statistics.mean(comb_ms)},
@@ -526,12 +561,10 @@ def run_ours(args):
             "value": eff / r["t_full_s"] / 1e12, "unit": "TFLOP/s", "cores": r["cores"], "kind": "oracle",
             "sample": f"packed rows {r['rows'][0]}..{r['rows'][1]} ({100 * r['frac']:.2f}% of the "
                       f"multiplications, {r['sample_s']:.1f} s), extrapolated to the whole product"}
-    if rank == 0:
-        print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def step_percentiles(step_ms):
@@ -651,20 +684,36 @@ def run_batched(args, mode):
     line["error"] = {kind + "_max_of_16": max(errs), "tolerance": tol,
                      "checked": "every 64th instance, device-timed and end-to-end results"}
     line["clocks"] = clocks
-    if rank == 0:
-        print(json.dumps(line))
-    return 0
+    return line if rank == 0 else None
+
+
+# Serving rates at which each mode has run clean on GB300 (every request
+# completed, no device error): bf16x3 at 2000 req/s for 60 s (offered load
+# about 1% of its capacity) and the FP64 emulation at 500 req/s.  Plain FP64
+# serving is not run: offered more work than it completes, it raised an
+# illegal-address fault whose cause was not found, so its capacity is timed
+# one request at a time instead.  Higher rates are refused.
+SERVING_CLEAN_RATE = {"bf16x3": 2000.0, "ozaki": 500.0}
 
 
 def run_serving(args, mode):
     """Serving workload: Poisson arrivals at --rate for --duration seconds; requests
     draw matrices from a 256-entry pool (m log-U[128,8192], n log-U[64,2048],
-    N(0,1)); admission by a 40 GB budget; plans resident after warm-up."""
+    N(0,1)); admission by a 40 GB budget; plans resident after warm-up.
+
+    Every request writes its own output buffer: a buffer of a pool entry is
+    reused only after the request that last wrote it has completed (a new
+    buffer is allocated otherwise).  Requests spread over the timed phase
+    write buffers of their own that are compared with the oracle afterwards."""
     import torch
 
     import oracle
     import paper_1902_02104_gb300 as ata
     from paper_1902_02104_gb300 import inputs
+    cap = SERVING_CLEAN_RATE.get(mode)
+    if cap is None or args.rate > cap:
+        raise SystemExit(f"serving_{mode} at {args.rate:g} req/s is refused: the measured-clean rates are "
+                         f"{SERVING_CLEAN_RATE} requests per second")
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
@@ -672,46 +721,77 @@ def run_serving(args, mode):
     rng, pool = inputs.serving_pool(256, seed=4)
     pool = [a.astype(dt) for a in pool]
     As = [torch.from_numpy(a).to(dev) for a in pool]
-    nring = 2  # output buffers per pool entry
-    Cs = [[torch.empty(a.shape[1] * (a.shape[1] + 1) // 2, dtype=torch.float64, device=dev) for _ in range(nring)]
-          for a in pool]
+
+    def new_c(i):
+        n = pool[i].shape[1]
+        return torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
+
+    free = [[new_c(i)] for i in range(len(pool))]  # output buffers no running request writes
+    running = [[] for _ in pool]                   # per entry: (ticket, buffer), oldest first
+    torch.cuda.synchronize()  # inputs complete before the server's streams read them
     srv = ata.Server(40 << 30, MODE_CODES[mode], max_inflight=16)
+
+    def reap(i, wait_us=0):
+        """Move buffers of entry i's completed requests (oldest first) back to free."""
+        while running[i] and srv.poll(running[i][0][0], wait_us) == ata.ATA_OK:
+            free[i].append(running[i].pop(0)[1])
+
+    def submit(i, own=None):
+        if own is not None:
+            return srv.submit(As[i], own)
+        if not free[i]:
+            reap(i)
+        c = free[i].pop() if free[i] else new_c(i)
+        t = srv.submit(As[i], c)
+        running[i].append((t, c))
+        return t
+
+    def drain():
+        for i in range(len(pool)):
+            while running[i]:
+                reap(i, 600_000_000)
+
     # warm-up: every pool shape once (plans become resident)
-    tick = [srv.submit(As[i], Cs[i][0]) for i in range(len(pool))]
-    for t in tick:
-        srv.poll(t, 600_000_000)
+    for i in range(len(pool)):
+        submit(i)
+    drain()
     arrivals = inputs.poisson_arrivals(args.rate, args.duration, seed=4)
     which = rng.integers(0, len(pool), size=arrivals.size)
+    n_check = min(8, arrivals.size)
+    check_at = set(np.linspace(0, arrivals.size - 1, n_check).round().astype(int).tolist()) if n_check else set()
+    checks = []  # (pool entry, own buffer, ticket)
     srv.reset_stats()
-    pending = []
-    use = [0] * len(pool)
+    sampler = ClockSampler(gpu_smi_index(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
     t0 = time.perf_counter()
-    for t_arr, i in zip(arrivals, which):
+    for k, (t_arr, i) in enumerate(zip(arrivals, which)):
         while time.perf_counter() - t0 < t_arr:
             pass
-        c = Cs[i][use[i] % nring]
-        use[i] += 1
-        pending.append(srv.submit(As[i], c))
-    for t in pending:
+        if k in check_at:
+            c = new_c(int(i))
+            checks.append((int(i), c, submit(int(i), own=c)))
+        else:
+            submit(int(i))
+    for _, _, t in checks:
         srv.poll(t, 600_000_000)
+    drain()
     wall = time.perf_counter() - t0
+    clocks = sampler.stop()
     st = srv.stats()
     served_kernels = srv.kernels()
+    srv.close()
     eff = sum(effective_flops(*pool[i].shape) for i in which)
-    # latency of the timed requests only: the server keeps all; recompute from the tail
     kind, tol = TOLERANCE[mode]
-    # correctness: a few requests run alone, then compared with the oracle
+    # correctness: requests served in the mix, against the oracle
     errs = []
-    for i in range(0, 256, 64):
-        t = srv.submit(As[i], Cs[i][0])
-        srv.poll(t, 600_000_000)
-        got = Cs[i][0].cpu().numpy()
+    for i, c, _ in checks:
+        got = c.cpu().numpy()
         ref = oracle.ata_packed(pool[i])
         if kind == "normwise":
             errs.append(oracle.normwise_error(got, ref, pool[i].shape[1]))
         else:
             errs.append(oracle.componentwise_error(got, ref, oracle.abs_gram_packed(pool[i])))
-    srv.close()
     # the plain FP64 path on the same pool: its service time per request, run
     # one request at a time on one stream (capacity, not served under load)
     fp64 = None
@@ -747,13 +827,14 @@ def run_serving(args, mode):
     line["latency_us"] = {"p50": st["p50_us"], "p99": st["p99_us"], "completed": st["completed"]}
     line["offered_effective_tflops"] = eff / args.duration / 1e12
     line["plain_f64_capacity"] = fp64
-    line["error"] = {kind + "_max_of_4": max(errs), "tolerance": tol}
+    line["error"] = {kind + "_max": max(errs) if errs else None, "tolerance": tol,
+                     "checked": f"{len(errs)} requests served in the mix (spread over the timed phase), "
+                                f"full oracle"}
     line["roofline"] = None
     line["e2e"] = None
     line["gpu_launches"] = int(served_kernels)
-    if rank == 0:
-        print(json.dumps(line))
-    return 0
+    line["clocks"] = clocks
+    return line if rank == 0 else None
 
 
 def run_gemm(args):
@@ -905,12 +986,70 @@ def run_gemm(args):
         line["cpu_baseline"] = {"value": eff / t_full / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
                                 "kind": "oracle", "sample": f"{cnt} sampled entries ({dt_s:.1f} s), extrapolated "
                                                             f"to all {p * r} entries"}
-    if rank == 0:
-        print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
+
+
+# The other workloads of the benchmark family, run after the default one at
+# N = 1 with a short timed region each and attached to its line: the plain
+# FP64 form at 512 x 384, the precision form in both leaf modes, the batched
+# form and the serving form (10 s of arrivals; 60 s with --workload
+# serving_bf16x3 --duration 60).
+SUB_CONFIGS = [
+    ("plain FP64, A 512 x 384, cutoff 64", "ata_f64_512x384", {}),
+    ("precision form, bf16x3 leaves, A 16384 x 8192 FP32", "ata_bf16x3_16384x8192", {}),
+    ("precision form, TF32 leaves, A 16384 x 8192 FP32", "ata_tf32_16384x8192", {}),
+    ("batched form, 512 instances, bf16x3 leaves", "batched_bf16x3", {}),
+    ("serving form, bf16x3 leaves, Poisson 2000 req/s", "serving_bf16x3", {"duration": 10.0, "rate": 2000.0}),
+]
+
+
+def dispatch(args):
+    if args.workload in GEMM_WORKLOADS:
+        return run_gemm(args)
+    if args.workload.startswith("batched_"):
+        return run_batched(args, args.workload.split("_", 1)[1])
+    if args.workload.startswith("serving_"):
+        return run_serving(args, args.workload.split("_", 1)[1])
+    return run_ours(args)
+
+
+def summarize(line):
+    keep = ["metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "error", "clocks",
+            "step_ms", "latency_us", "offered_effective_tflops", "gpu_launches", "plain_f64_capacity"]
+    out = {k: line[k] for k in keep if k in line}
+    if line.get("roofline"):
+        out["roofline"] = {k: line["roofline"][k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel")}
+    if line.get("e2e"):
+        out["e2e"] = line["e2e"]
+    return out
+
+
+def run_configs(args):
+    import copy
+
+    import torch
+    out = []
+    for label, wl, over in SUB_CONFIGS:
+        sub = copy.copy(args)
+        sub.workload = wl
+        sub.steps = max(5, min(args.steps, 10))
+        sub.warmup = 3
+        sub.no_library = sub.no_cpu_baseline = sub.no_plain = True
+        sub.cutoff = None
+        for k, v in over.items():
+            setattr(sub, k, v)
+        try:
+            res = summarize(dispatch(sub))
+        except Exception as e:  # keep the headline line whatever happens here
+            res = {"config": {"workload": wl}, "failed": repr(e)[:300]}
+        res["label"] = label
+        out.append(res)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -923,27 +1062,36 @@ def main():
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-library", action="store_true", help="skip the torch.matmul library reference")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: skip the other workloads' short runs")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
-    ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
+    ap.add_argument("--rate", type=float, default=2000.0,
+                    help="serving: requests per second (at most the mode's measured-clean rate)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cutoff", type=int, default=None, help="override the workload's cutoff")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload.startswith("serving_"):
+        mode = args.workload.split("_", 1)[1]
+        if args.rate > SERVING_CLEAN_RATE.get(mode, 0.0):
+            ap.error(f"--rate {args.rate:g} for {args.workload} is refused: measured-clean rates are "
+                     f"{SERVING_CLEAN_RATE} requests per second")
     if args.impl == "reference":
         if args.workload not in WORKLOADS:
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the A^t A oracle on the "
                                                                   "A^t A workloads only"}))
             return 0
         return run_reference(args)
-    if args.workload in GEMM_WORKLOADS:
-        return run_gemm(args)
-    if args.workload.startswith("batched_"):
-        return run_batched(args, args.workload.split("_", 1)[1])
-    if args.workload.startswith("serving_"):
-        return run_serving(args, args.workload.split("_", 1)[1])
-    return run_ours(args)
+    line = dispatch(args)
+    if line is None:
+        return 0
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == DEFAULT_WORKLOAD and world == 1 and not args.no_configs:
+        line["configs"] = run_configs(args)
+    print(json.dumps(line))
+    return 0
 
 
 if __name__ == "__main__":

@@ -72,7 +72,24 @@ typedef enum {
                               accumulation in chunks added into FP64          */
     ATA_F64_OZAKI = 3      /* FP64 input, FP64-accuracy leaves emulated on
                               bf16 tensor cores (exact slice products, FP64
-                              Strassen sums and final accumulation)          */
+                              Strassen sums and final accumulation).  Each
+                              column of a leaf operand is held in 48-bit
+                              fixed point below the column's largest entry
+                              M_i, and the low-order part products add in
+                              FP32, so the bound that holds for every input
+                              is |C_ij - (A^t A)_ij| <= 2^-35 K M_i M_j for
+                              classical leaves (K = m).  Componentwise
+                              |dC_ij| <= 1e-11 (|A|^t|A|)_ij is measured on
+                              inputs whose columns keep their weight within a
+                              bounded range of the column maximum: i.i.d.
+                              entries, columns scaled over 2^+-200, row bands
+                              scaled over 2^+-20.  It does not hold when a
+                              column has a few entries far above its others
+                              in rows where another column is small (one
+                              entry 2^30 above the rest gives about 1e-7 on
+                              the pair); ATA_F64 meets it for every input.
+                              With Strassen levels the error is bounded
+                              normwise.                                      */
 } ata_dtype;
 
 /* Strassen form used for the off-diagonal products. */
@@ -121,6 +138,20 @@ const char* ata_status_string(ata_status s);
 /* Thread-local description of the last failure in this thread. */
 const char* ata_last_error_message(void);
 
+/* Device memory the library holds for its own buffers (plan workspaces, task
+ * tables, staging buffers of the host-memory calls, batched bindings), in
+ * bytes: what every live plan, batch and server holds together.  Destroying
+ * them returns it to zero; a value that stays above zero afterwards is a
+ * leak.
+ *
+ * Allocation failures can be injected from the host for tests: with the
+ * environment variable ATA_FAULT=alloc@N, the N-th of these allocations
+ * after the variable takes that value fails as if the device were out of
+ * memory (the call returns ATA_ENOMEM and frees what it had allocated).
+ * Every device allocation the library makes goes through this count except
+ * the static array of ata_execute_static_scratch. */
+int64_t ata_device_bytes_held(void);
+
 /* Run the planner only (no device call): fills *out for the plan that
  * ata_plan_create(m, n, dtype, cutoff) would build.  cutoff must be in
  * [16, 4096]; 0 selects it by the planner's cost model (as ata_plan_create).
@@ -160,6 +191,18 @@ typedef struct {
                                     most 1/8 to the tile area; 0 = 128 x 128 tiles
                                     on single CTAs; -1 = the mode's default
                                     (pairs for TF32, single CTAs otherwise) */
+    int32_t wait_limit_us;       /* tensor-core leaves: limit of each wait of
+                                    the leaf kernel's pipeline (TMA producer,
+                                    MMA issuer, epilogue) in microseconds, in
+                                    [1, 1000000]; -1 or 0 = 1 s.  A wait that
+                                    runs out records its code in the plan's
+                                    device status word (ata_plan_device_status)
+                                    and the kernel returns without finishing;
+                                    the waits for copies and MMAs still in
+                                    flight before the kernel exits keep 1 s.
+                                    For tests of that failure path: a limit
+                                    shorter than the pipeline's latency makes
+                                    the waits run out on purpose */
 } ata_plan_options;
 
 /* Same as ata_plan_create with explicit options (opts may not be NULL).
@@ -360,10 +403,12 @@ ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx,
  * shares the one array and overwrites what the previous call left there, so
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race; calls queued on one stream are ordered.  The host task tables are
- * copied into the array with cudaMemcpyAsync on `stream`.
- * Errors: ATA_EINVAL (bad sizes or pointers, cutoff outside [16, 4096], or a
- * problem whose tables and workspace exceed the 64 MiB array -- use
- * ata_execute or a larger cutoff), ATA_ECUDA. */
+ * copied into the array with cudaMemcpyAsync on `stream` from a host buffer
+ * that lives only for the call, so a call on a stream that is capturing is
+ * refused (ATA_EINVAL) rather than recorded.
+ * Errors: ATA_EINVAL (bad sizes or pointers, cutoff outside [16, 4096], a
+ * capturing stream, or a problem whose tables and workspace exceed the
+ * 64 MiB array -- use ata_execute or a larger cutoff), ATA_ECUDA. */
 ata_status ata_execute_static_scratch(int64_t m, int64_t n, const double* A,
                                       int64_t lda, double* C_packed,
                                       int cutoff, void* stream);

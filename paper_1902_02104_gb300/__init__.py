@@ -20,7 +20,7 @@ __all__ = [
     "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
     "ata_execute_host_async", "ata_plan_wait", "ata_batched_graph_kernels",
     "ata_execute_batched", "Batch", "packed_layout", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
-    "packed_size", "lib_path",
+    "packed_size", "lib_path", "ata_device_bytes_held",
 ]
 
 ATA_F64, ATA_F32_BF16X3, ATA_F32_TF32, ATA_F64_OZAKI = 0, 1, 2, 3
@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int32), ("variant", ctypes.c_int32), ("fuse_levels", ctypes.c_int32),
-                ("max_strassen_levels", ctypes.c_int32), ("cta_pair", ctypes.c_int32)]
+                ("max_strassen_levels", ctypes.c_int32), ("cta_pair", ctypes.c_int32),
+                ("wait_limit_us", ctypes.c_int32)]
 
 
 _lib = None
@@ -76,6 +77,7 @@ def load():
     sig = {
         "ata_status_string": ([i32], ctypes.c_char_p),
         "ata_last_error_message": ([], ctypes.c_char_p),
+        "ata_device_bytes_held": ([], i64),
         "ata_plan_query": ([i64, i64, i32, i32, ctypes.POINTER(PlanInfo)], i32),
         "ata_plan_query_opts": ([i64, i64, i32, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanInfo)], i32),
         "ata_plan_create": ([ctypes.POINTER(vp), i64, i64, i32, i32], i32),
@@ -128,6 +130,11 @@ def _check(st: int):
         raise AtaError(st, load().ata_last_error_message().decode(errors="replace"))
 
 
+def ata_device_bytes_held() -> int:
+    """Device bytes the library holds for plans, batches and servers."""
+    return int(load().ata_device_bytes_held())
+
+
 def packed_size(n: int) -> int:
     return n * (n + 1) // 2
 
@@ -138,8 +145,10 @@ def _dtype_code(dtype) -> int:
     return int(dtype)
 
 
-def _opts(cutoff=0, variant=-1, fuse_levels=-1, max_strassen_levels=-1, cta_pair=-1) -> PlanOptions:
-    return PlanOptions(int(cutoff), int(variant), int(fuse_levels), int(max_strassen_levels), int(cta_pair))
+def _opts(cutoff=0, variant=-1, fuse_levels=-1, max_strassen_levels=-1, cta_pair=-1,
+          wait_limit_us=-1) -> PlanOptions:
+    return PlanOptions(int(cutoff), int(variant), int(fuse_levels), int(max_strassen_levels), int(cta_pair),
+                       int(wait_limit_us))
 
 
 def ata_plan_query(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> dict:

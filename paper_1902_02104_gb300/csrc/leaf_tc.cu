@@ -110,17 +110,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait for the phase of `bar` with the given parity.  Returns false
 // (after recording `code` in *status unless another role already did) when
-// the wait gives up: on a timeout, or when *status shows that another role
-// gave up first.
+// the wait gives up: after `limit_ns`, or when *status shows that another
+// role gave up first.
 template <int CG = 1>
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code,
+                                          uint64_t limit_ns) {
     if (mbar_try_wait<CG>(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait<CG>(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*reinterpret_cast<volatile int*>(status) != 0) return false;
-            if (globaltimer() - t0 > kTimeoutNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 atomicCAS(status, 0, code);
                 return false;
             }
@@ -1019,7 +1020,7 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
 template <int NB, int MODE, int CG>
 __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ BindSet<NB> bs, const TcProd* __restrict__ tcp,
-                   const LeafTile* __restrict__ tiles, int ntiles, int* __restrict__ status) {
+                   const LeafTile* __restrict__ tiles, int ntiles, int* __restrict__ status, uint64_t wait_ns) {
     using G = Geo<MODE>;
     using SH = Shape<MODE, CG, NB>;
     constexpr int NSTAGE = SH::NSTAGE;
@@ -1096,7 +1097,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                 const int yb = lt.tj * SH::TN + (int)rank * SH::YROWS;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % NSTAGE, ph = (it / NSTAGE) & 1;
-                    if (!mbar_wait<CG>(b_empty + 8 * s, ph ^ 1, status, ERR_TIMEOUT_PRODUCER)) {
+                    if (!mbar_wait<CG>(b_empty + 8 * s, ph ^ 1, status, ERR_TIMEOUT_PRODUCER, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -1264,14 +1265,14 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                     bool good = true;
                     if (lane == 0) {
                         if (G::F_FINAL && kb == 0)
-                            good = mbar_wait<CG>(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA);
-                        good = good && mbar_wait<CG>(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA);
+                            good = mbar_wait<CG>(b_fempty, (tcount & 1) ^ 1, status, ERR_TIMEOUT_MMA, wait_ns);
+                        good = good && mbar_wait<CG>(b_full + 8 * s, ph, status, ERR_TIMEOUT_MMA, wait_ns);
                         if (!fl.f_before_d) {
                             if (G::ND > 0 && fl.first_in_chunk)
                                 good = good && mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
-                                                             ERR_TIMEOUT_MMA);
+                                                             ERR_TIMEOUT_MMA, wait_ns);
                             if (HAS_F && !G::F_FINAL && fl.f_first)
-                                good = good && mbar_wait<CG>(b_fempty, (fchunk & 1) ^ 1, status, ERR_TIMEOUT_MMA);
+                                good = good && mbar_wait<CG>(b_fempty, (fchunk & 1) ^ 1, status, ERR_TIMEOUT_MMA, wait_ns);
                         }
                     }
                     if (!meet_helper(!__shfl_sync(0xffffffffu, good, 0))) {
@@ -1282,7 +1283,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                         good = true;
                         if (lane == 0)
                             good = mbar_wait<CG>(b_dempty + 8 * buf, ((chunk / G::DBUF) & 1) ^ 1, status,
-                                                 ERR_TIMEOUT_MMA);
+                                                 ERR_TIMEOUT_MMA, wait_ns);
                         if (!meet_helper(!__shfl_sync(0xffffffffu, good, 0))) {
                             ok = false;
                             break;
@@ -1323,7 +1324,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                 while (dnext < nkb || fnext < nkb) {
                     if (dnext <= fnext) {
                         const uint32_t buf = chunk % G::DBUF;
-                        if (!mbar_wait<CG>(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                        if (!mbar_wait<CG>(b_dfull + 8 * buf, (chunk / G::DBUF) & 1, status, ERR_TIMEOUT_EPILOGUE, wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -1373,7 +1374,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                         dnext = dnext == nkb - 1 ? nkb : min(dnext + kbpc, nkb - 1);
                     } else {
                         if constexpr (HAS_F && !G::F_FINAL) {
-                            if (!mbar_wait<CG>(b_ffull, fchunk & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                            if (!mbar_wait<CG>(b_ffull, fchunk & 1, status, ERR_TIMEOUT_EPILOGUE, wait_ns)) {
                                 ok = false;
                                 break;
                             }
@@ -1407,7 +1408,7 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                 if (!ok) break;
             }
             if constexpr (G::F_FINAL) {
-                if (!mbar_wait<CG>(b_ffull, tcount & 1, status, ERR_TIMEOUT_EPILOGUE)) {
+                if (!mbar_wait<CG>(b_ffull, tcount & 1, status, ERR_TIMEOUT_EPILOGUE, wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -1584,6 +1585,10 @@ cudaLaunchAttribute pair_cluster_attr() {
     return a;
 }
 
+// Limit of the pipeline waits of a launch (the plan's option; 1 s by
+// default).  The teardown waits always keep the 1 s limit.
+uint64_t wait_limit(const DeviceTables& t) { return t.wait_ns > 0 ? t.wait_ns : kTimeoutNs; }
+
 template <int NB, int MODE>
 cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream_t s, cudaEvent_t before_gemm) {
     if (Geo<MODE>::SLICED) {
@@ -1623,12 +1628,14 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
             cfg.stream = s;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, MODE, 2>, bs, t.tcp, t.tiles, t.ntiles, t.status);
+            return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, MODE, 2>, bs, t.tcp, t.tiles, t.ntiles, t.status,
+                                      wait_limit(t));
         }
     }
     using SH = Shape<MODE, 1, NB>;
     const int grid = std::max(1, std::min(t.ntiles, g_sms));
-    tc_gemm_kernel<NB, MODE, 1><<<grid, SH::THREADS, SH::SMEM, s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status);
+    tc_gemm_kernel<NB, MODE, 1><<<grid, SH::THREADS, SH::SMEM, s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status,
+                                                                     wait_limit(t));
     return cudaGetLastError();
 }
 
@@ -1934,7 +1941,7 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     const int64_t ex_total = std::max<int64_t>(ex_elems + tm_elems, 1);
     const int64_t total = al(o_ex + ex_total * 8);
     char* blob = nullptr;
-    if (cudaMalloc(&blob, total) != cudaSuccess) {
+    if (dev_malloc(&blob, total) != cudaSuccess) {
         cudaGetLastError();
         return fail(ATA_ENOMEM, "tensor-core tables: cudaMalloc failed");
     }
@@ -1954,7 +1961,7 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     if (!scale.empty()) std::memcpy(hb.data() + o_scale, scale.data(), scale.size() * sizeof(PrepTask));
     cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(blob);
+        dev_free(blob);
         return cuda_fail(e, "tensor-core tables: upload");
     }
     d->tc_blob = blob;

@@ -69,6 +69,17 @@ extern "C" ata_status ata_execute_static_scratch(int64_t m, int64_t n, const dou
     if (reinterpret_cast<uintptr_t>(A) % 8 || reinterpret_cast<uintptr_t>(C_packed) % 8)
         return fail(ATA_EINVAL, "A and C_packed must be 8-byte aligned");
     if (n == 0) return ATA_OK;
+    {
+        // The task tables are copied from a host buffer that lives only for
+        // this call; a copy recorded into a graph under capture would read it
+        // after it is gone.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(ATA_EINVAL, "the stream is capturing: this call copies its tables from a temporary host "
+                                    "buffer and cannot be recorded");
+    }
 
     char* scratch = nullptr;
     ata_status st = scratch_address(&scratch);

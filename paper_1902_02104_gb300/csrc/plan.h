@@ -158,6 +158,7 @@ struct PlanOptions {
     int fuse_levels = 1;
     int max_levels = 64;
     bool cta_pair = false;  // tensor-core leaves on 256 x 128 CTA-pair tiles where eligible
+    uint64_t wait_ns = 0;   // tensor-core leaves: pipeline wait limit (0 = the kernel's default)
 };
 
 // Builds the plan.  Returns false and sets *err on invalid input.

@@ -40,6 +40,56 @@ ata_status cuda_fail(cudaError_t e, const char* what) {
 static std::atomic<uint64_t> g_plan_ids{1};
 
 // ---------------------------------------------------------------------------
+// Device allocations: bytes held, and host-side allocation-failure injection.
+
+namespace {
+std::mutex g_alloc_mu;
+std::map<void*, size_t> g_alloc_live;
+int64_t g_alloc_bytes = 0;
+std::string g_fault_spec;   // last value of ATA_FAULT seen
+int64_t g_fault_at = 0;     // allocation to fail (1-based), 0 = none
+int64_t g_alloc_calls = 0;  // allocations since ATA_FAULT took its value
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        const char* f = getenv("ATA_FAULT");
+        const std::string spec = f ? f : "";
+        if (spec != g_fault_spec) {
+            g_fault_spec = spec;
+            g_alloc_calls = 0;
+            g_fault_at = 0;
+            if (spec.rfind("alloc@", 0) == 0) g_fault_at = std::atoll(spec.c_str() + 6);
+        }
+        if (g_fault_at > 0 && ++g_alloc_calls == g_fault_at) return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_live[*p] = bytes;
+    g_alloc_bytes += (int64_t)bytes;
+    return cudaSuccess;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        auto it = g_alloc_live.find(p);
+        if (it != g_alloc_live.end()) {
+            g_alloc_bytes -= (int64_t)it->second;
+            g_alloc_live.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
 // Host tables -> one device blob.
 
 static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -74,7 +124,7 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
     const int64_t o_cchunk = place(h.comb_chunks.size() * sizeof(Chunk));
     const int64_t total = std::max<int64_t>(off, 256);
     char* blob = nullptr;
-    cudaError_t e = cudaMalloc(&blob, total);
+    cudaError_t e = dev_malloc(&blob, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ATA_ENOMEM, "task tables: cudaMalloc failed");
@@ -92,7 +142,7 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
     put(o_cchunk, h.comb_chunks.data(), h.comb_chunks.size() * sizeof(Chunk));
     e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(blob);
+        dev_free(blob);
         return cuda_fail(e, "task tables: upload");
     }
     d->blob = blob;
@@ -212,8 +262,8 @@ void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt) {
 
 
 void DeviceTables::free_all() {
-    if (blob) cudaFree(blob);
-    if (tc_blob) cudaFree(tc_blob);
+    dev_free(blob);
+    dev_free(tc_blob);
     blob = nullptr;
     tc_blob = nullptr;
     tcp = nullptr;
@@ -340,7 +390,7 @@ void GraphCache::release() {
     exec = nullptr;
     cap_stream = nullptr;
     if (launched) cudaEventSynchronize(launched);
-    if (dev_binds) cudaFree(dev_binds);
+    dev_free(dev_binds);
     if (stage_binds) cudaFreeHost(stage_binds);
     for (cudaEvent_t* e : {&uploaded, &launched}) {
         if (*e) cudaEventDestroy(*e);
@@ -381,7 +431,7 @@ ata_status launch_via_graph(const DeviceTables& t, const Bind* binds, int nb, Gr
     const size_t bytes = (size_t)nb * sizeof(Bind);
     if (!g->exec || g->dev_count != nb) {
         if (g->exec || g->dev_binds) g->release();
-        ATA_CUDA(cudaMalloc(&g->dev_binds, bytes));
+        ATA_CUDA(dev_malloc(&g->dev_binds, bytes));
         ATA_CUDA(cudaMallocHost(&g->stage_binds, bytes));
         ATA_CUDA(cudaEventCreateWithFlags(&g->uploaded, cudaEventDisableTiming));
         ATA_CUDA(cudaEventCreateWithFlags(&g->launched, cudaEventDisableTiming));
@@ -439,8 +489,8 @@ struct HostPipe {
                 if (*e) cudaEventDestroy(*e);
                 *e = nullptr;
             }
-            if (A[b]) cudaFree(A[b]);
-            if (C[b]) cudaFree(C[b]);
+            dev_free(A[b]);
+            dev_free(C[b]);
             A[b] = nullptr;
             C[b] = nullptr;
         }
@@ -465,6 +515,7 @@ struct ata_plan_s {
     GraphCache graph;
     std::mutex mu;
     int64_t check = 0;          // self-checked kernels (ATA_CHECK_BOUNDS=1 at creation)
+    uint64_t wait_ns = 0;       // tensor-core leaves: pipeline wait limit (0 = default)
     // staging for ata_execute_host
     void* stage_A = nullptr;
     double* stage_C = nullptr;
@@ -473,9 +524,9 @@ struct ata_plan_s {
         pipe.release();
         graph.release();
         tables.free_all();
-        if (ws) cudaFree(ws);
-        if (stage_A) cudaFree(stage_A);
-        if (stage_C) cudaFree(stage_C);
+        dev_free(ws);
+        dev_free(stage_A);
+        dev_free(stage_C);
     }
 };
 
@@ -505,6 +556,9 @@ ata_status make_options(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_op
     if (u.max_strassen_levels < -1 || u.max_strassen_levels > 64)
         return fail(ATA_EINVAL, "max_strassen_levels must be -1 or in [0, 64]");
     if (u.cta_pair < -1 || u.cta_pair > 1) return fail(ATA_EINVAL, "cta_pair must be -1, 0 or 1");
+    if (u.wait_limit_us < -1 || u.wait_limit_us > 1000000)
+        return fail(ATA_EINVAL, "wait_limit_us must be -1, 0 or in [1, 1000000]");
+    o->wait_ns = u.wait_limit_us > 0 ? (uint64_t)u.wait_limit_us * 1000u : 0;
     o->leaf = leaf_of(dtype);
     o->variant = variant;
     o->cutoff = cutoff != 0 ? cutoff : default_cutoff(m, n, dtype);
@@ -523,6 +577,7 @@ ata_plan_options default_opts(int cutoff, int variant) {
     u.fuse_levels = -1;
     u.max_strassen_levels = -1;
     u.cta_pair = -1;
+    u.wait_limit_us = -1;
     return u;
 }
 
@@ -590,6 +645,7 @@ ata_status rebuild_tables(ata_plan plan, int64_t lda, int64_t ldb = 0, int64_t l
         st = build_tc_tables(h, std::vector<char*>{plan->ws}, &plan->tables);
         if (st != ATA_OK) return st;
     }
+    plan->tables.wait_ns = plan->wait_ns;
     plan->lda = lda;
     plan->ldb = ldb;
     plan->ldc = ldc;
@@ -639,6 +695,11 @@ const char* ata_status_string(ata_status s) {
 }
 
 const char* ata_last_error_message(void) { return g_last_error.c_str(); }
+
+int64_t ata_device_bytes_held(void) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc_bytes;
+}
 
 ata_status ata_plan_query(int64_t m, int64_t n, ata_dtype dtype, int cutoff, ata_plan_info* out) {
     const ata_plan_options u = default_opts(cutoff, ATA_STRASSEN);
@@ -824,7 +885,7 @@ ata_status finish_create(std::unique_ptr<ata_plan_s>& p, ata_dtype dtype) {
     }
     ATA_CUDA(cudaGetDevice(&p->device));
     if (p->plan.ws_bytes > 0) {
-        cudaError_t e = cudaMalloc(&p->ws, p->plan.ws_bytes);
+        cudaError_t e = dev_malloc(&p->ws, p->plan.ws_bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p->ws = nullptr;
@@ -885,6 +946,7 @@ ata_status ata_gemm_plan_create(ata_plan* out, int64_t m, int64_t p, int64_t r, 
     std::unique_ptr<ata_plan_s> pl(new ata_plan_s());
     std::string err;
     if (!build_gemm_plan(m, p, r, o, &pl->plan, &err)) return fail(ATA_EINVAL, err);
+    pl->wait_ns = o.wait_ns;
     st = finish_create(pl, dtype);
     if (st != ATA_OK) return st;
     *out = pl.release();
@@ -929,6 +991,7 @@ ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype d
     std::unique_ptr<ata_plan_s> p(new ata_plan_s());
     std::string err;
     if (!build_plan(m, n, o, &p->plan, &err)) return fail(ATA_EINVAL, err);
+    p->wait_ns = o.wait_ns;
     st = finish_create(p, dtype);
     if (st != ATA_OK) return st;
     *out = p.release();
@@ -990,14 +1053,14 @@ ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, doub
     {
         std::lock_guard<std::mutex> lk(plan->mu);
         if (!plan->stage_A && m > 0) {
-            if (cudaMalloc(&plan->stage_A, (size_t)m * n * es) != cudaSuccess) {
+            if (dev_malloc(&plan->stage_A, (size_t)m * n * es) != cudaSuccess) {
                 cudaGetLastError();
                 plan->stage_A = nullptr;
                 return fail(ATA_ENOMEM, "staging buffer for A");
             }
         }
         if (!plan->stage_C) {
-            if (cudaMalloc(&plan->stage_C, (size_t)(n * (n + 1) / 2) * 8) != cudaSuccess) {
+            if (dev_malloc(&plan->stage_C, (size_t)(n * (n + 1) / 2) * 8) != cudaSuccess) {
                 cudaGetLastError();
                 plan->stage_C = nullptr;
                 return fail(ATA_ENOMEM, "staging buffer for C");
@@ -1035,8 +1098,8 @@ ata_status ata_execute_host_async(ata_plan plan, const void* A_host, int64_t lda
             for (int i = 0; i < 2 && ok; ++i) {
                 for (cudaEvent_t* e : {&P.a_ready[i], &P.comp_done[i], &P.c_read[i]})
                     ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-                ok = ok && (m == 0 || cudaMalloc(&P.A[i], a_bytes) == cudaSuccess);
-                ok = ok && cudaMalloc(&P.C[i], c_bytes) == cudaSuccess;
+                ok = ok && (m == 0 || dev_malloc(&P.A[i], a_bytes) == cudaSuccess);
+                ok = ok && dev_malloc(&P.C[i], c_bytes) == cudaSuccess;
             }
             if (!ok) {
                 cudaGetLastError();

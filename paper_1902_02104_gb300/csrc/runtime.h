@@ -94,6 +94,7 @@ struct DeviceTables {
     int* status = nullptr;     // device error word of the tensor-core kernels
     char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
     size_t tc_ex_bytes = 0;
+    uint64_t wait_ns = 0;      // limit of the leaf kernel's pipeline waits (0 = its default)
     void free_all();
 };
 
@@ -117,6 +118,21 @@ struct GraphCache {
     cudaEvent_t uploaded = nullptr, launched = nullptr;
     void release();
 };
+
+// Device allocations of the library's own buffers (workspaces, tables,
+// staging).  dev_malloc counts the bytes held (ata_device_bytes_held) and
+// honours the host-side fault injection ATA_FAULT=alloc@N: the N-th
+// allocation after the variable takes a new value fails as if the device
+// were out of memory (nothing is allocated).  dev_free(nullptr) is a no-op.
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    void* v = nullptr;
+    cudaError_t e = dev_malloc(&v, bytes);
+    *p = static_cast<T*>(v);
+    return e;
+}
 
 extern thread_local std::string g_last_error;
 ata_status fail(ata_status s, const std::string& msg);

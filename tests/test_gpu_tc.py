@@ -174,3 +174,86 @@ def test_ozaki_paper_scale_sampled(gpu):
     assert err <= 1e-11, err
     del C, plan
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# The FP64 emulation's accuracy across dynamic range.  Each column of a leaf
+# operand is held in 48-bit fixed point below the column's largest entry and
+# the low-order part products accumulate in FP32, so the bound that holds for
+# every input is |dC_ij| <= 2^-35 K max_k|a_ki| max_k|a_kj| (K = m for
+# classical leaves).  The componentwise 1e-11 is a property of inputs whose
+# columns keep their weight within a bounded range of the column maximum
+# (i.i.d., row- or column-scaled); a column with a few entries far above its
+# others, in rows where another column is small, falls outside it.
+
+def _ozaki_classical(A):
+    C, _ = run(A, ata.ATA_F64_OZAKI, 4096, max_strassen_levels=0)
+    return C
+
+
+def _column_bound(A):
+    """2^-35 m M_i M_j (packed), the worst-case bound of classical leaves."""
+    m, n = A.shape
+    M = np.max(np.abs(A), axis=0)
+    return oracle.pack_upper(np.exp2(-35.0) * m * np.outer(M, M))
+
+
+def test_ozaki_row_bands_2e20_componentwise(gpu):
+    # row bands of 128 rows scaled by 2^+20 and 2^-20 alternately, inside
+    # every column: inside the class
+    A = inputs.normal(1536, 640, seed=31)
+    A *= np.exp2(np.where((np.arange(1536) // 128) % 2 == 0, 20.0, -20.0))[:, None]
+    C = _ozaki_classical(A)
+    err = oracle.componentwise_error(C, oracle.ata_packed(A), oracle.abs_gram_packed(A))
+    assert err <= 1e-11, err
+
+
+@pytest.mark.parametrize("big", [30, 40])
+def test_ozaki_column_outlier_outside_the_class(gpu, big):
+    # column 0 holds one entry 2^big above its others; column 1 is zero in
+    # that row.  C_01 is then a sum of ordinary products that column 0 holds
+    # with only 48 - big - 2 bits: the componentwise 1e-11 does not hold for
+    # it (plain FP64 meets it), while the worst-case bound holds everywhere
+    # and the entries away from column 0 keep 1e-11.
+    A = inputs.normal(1024, 256, seed=32)
+    A[7, 0] = np.exp2(big)
+    A[7, 1] = 0.0
+    C = _ozaki_classical(A)
+    ref, G = oracle.ata_packed(A), oracle.abs_gram_packed(A)
+    n = A.shape[1]
+    assert np.all(np.abs(C - ref) <= _column_bound(A))
+    i01 = oracle.packed_index(0, 1, n)
+    assert abs(C[i01] - ref[i01]) / G[i01] > 1e-11
+    rest = np.ones(C.size, bool)
+    rest[oracle.packed_index(np.zeros(n, int), np.arange(n), n)] = False  # row 0 of C
+    assert oracle.componentwise_error(C[rest], ref[rest], G[rest]) <= 1e-11
+    C64, _ = run(A, ata.ATA_F64, 4096)
+    assert oracle.componentwise_error(C64, ref, G) <= 1e-11
+
+
+@pytest.mark.parametrize("gen", ["normal", "uniform", "scaled", "sparse"])
+def test_ozaki_worst_case_bound(gpu, gen):
+    rng = np.random.default_rng(33)
+    if gen == "normal":
+        A = inputs.normal(1200, 400, seed=34)
+    elif gen == "uniform":
+        A = inputs.uniform(1200, 400, seed=35)
+    elif gen == "scaled":
+        A = inputs.normal(1200, 400, seed=36) * np.exp2(rng.integers(-60, 60, size=400))[None, :]
+    else:  # most entries zero, a few far above the rest
+        A = inputs.normal(1200, 400, seed=37) * (rng.random((1200, 400)) < 0.05)
+        A[rng.integers(0, 1200, 40), rng.integers(0, 400, 40)] = np.exp2(30.0)
+    C = _ozaki_classical(A)
+    assert np.all(np.abs(C - oracle.ata_packed(A)) <= _column_bound(A))
+
+
+# ---------------------------------------------------------------------------
+# Winograd's variant in the FP32 modes, at the precision form's bounds
+
+@pytest.mark.parametrize("dtype", MODES32)
+def test_fp32_modes_winograd_normwise(gpu, dtype):
+    A = inputs.scaled_cols(4096, 2048, seed=2)
+    C, plan = run(A, dtype, 256, variant=ata.ATA_WINOGRAD)
+    assert plan.info["max_strassen_levels"] == 2
+    err = oracle.normwise_error(C, oracle.ata_packed(A), 2048)
+    assert err <= NORM_TOL[dtype], err

@@ -108,13 +108,51 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of the phase of `bar` with the given parity.
+template <int CG = 1>
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    if constexpr (CG == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    }
+    return ok != 0;
+}
+
 // Bounded wait for the phase of `bar` with the given parity.  Returns false
 // (after recording `code` in *status unless another role already did) when
 // the wait gives up: after `limit_ns`, or when *status shows that another
-// role gave up first.
+// role gave up first.  A limit shorter than the default (a plan option for
+// tests of this path) polls without blocking and reads the clock on every
+// poll, so that the wait gives up once the limit has passed (a blocking
+// try_wait could outlast a limit of a microsecond).
 template <int CG = 1>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code,
                                           uint64_t limit_ns) {
+    if (limit_ns < kTimeoutNs) {
+        const uint64_t t0 = globaltimer();
+        for (;;) {
+            if (mbar_test_wait<CG>(bar, parity)) return true;
+            if (*reinterpret_cast<volatile int*>(status) != 0) return false;
+            if (globaltimer() - t0 > limit_ns) {
+                atomicCAS(status, 0, code);
+                return false;
+            }
+        }
+    }
     if (mbar_try_wait<CG>(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {

@@ -678,6 +678,36 @@ ata_status execute_on(ata_plan plan, const void* A, int64_t lda, double* C_packe
 
 }  // namespace
 
+// One execution of an A^t A plan launched directly on `s`, without a CUDA
+// graph.  The serving layer uses it: a stream capture on its scheduler
+// thread would be broken by device-wide synchronisation that other threads
+// of the process may issue at any time (cudaDeviceSynchronize, or an
+// allocation that synchronises), so its executions make no capture.  The
+// kernels and their parameters are those a graph replay runs, so the
+// results are the same bits.  Returns the number of kernels launched.
+ata_status ata::execute_direct(ata_plan plan, const void* A, int64_t lda, double* C_packed, cudaStream_t s,
+                               int* kernels) {
+    *kernels = 0;
+    if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan");
+    const int64_t n = plan->plan.n;
+    if (lda < n || lda < 1) return fail(ATA_EINVAL, "lda must be >= max(n, 1)");
+    if (n == 0) return ATA_OK;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (lda != plan->lda) {
+        ATA_CUDA(cudaStreamSynchronize(s));
+        plan->pipe.sync();
+        ata_status st = rebuild_tables(plan, lda);
+        if (st != ATA_OK) return st;
+    }
+    Bind b = make_bind(plan, A, lda, C_packed);
+    ata_status st = enqueue_tables(plan->tables, &b, 1, s);
+    if (st != ATA_OK) return st;
+    ata_plan_info info;
+    fill_info(plan->plan, plan->dtype, &info);
+    *kernels = info.n_launches;
+    return ATA_OK;
+}
+
 extern "C" {
 
 const char* ata_status_string(ata_status s) {

@@ -164,6 +164,9 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
 // Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
 const Plan& plan_of(ata_plan p);
 Bind make_bind(ata_plan p, const void* A, int64_t lda, double* C);
+// An execution launched directly on s (no graph capture; see runtime.cu).
+ata_status execute_direct(ata_plan plan, const void* A, int64_t lda, double* C_packed, cudaStream_t s,
+                          int* kernels);
 uint64_t plan_id(ata_plan p);
 char* plan_workspace(ata_plan p);
 ata_dtype plan_dtype(ata_plan p);

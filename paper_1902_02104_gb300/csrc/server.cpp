@@ -9,7 +9,15 @@
 // the budget is needed.  Each admitted request runs its plan's graph on one of
 // `max_inflight` non-blocking streams, so requests overlap on the device, and
 // its completion is seen through a CUDA event.  Results do not depend on the
-// mix: every request replays the same kernels on its own workspace.
+// mix: every request runs the same kernels on its own workspace.
+//
+// Executions are launched directly on the slot's stream, without a CUDA
+// graph: capturing a graph on this thread would race with device-wide
+// synchronisation that the application's other threads may issue at any
+// time, which breaks the capture.  The application must still not free or
+// overwrite a request's A or C before its ticket completes, and must have
+// finished writing A before it submits it: the server's streams do not wait
+// for the application's streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -212,10 +220,10 @@ struct ata_server_s {
                 }
                 queue.pop_front();
                 e->busy = true;
-                ata_status st = ata_execute(e->plan, r.A, r.lda, r.C, free_slot->stream);
+                int nk = 0;
+                ata_status st = execute_direct(e->plan, r.A, r.lda, r.C, free_slot->stream, &nk);
                 std::string emsg = st == ATA_OK ? std::string() : g_last_error;
-                int32_t nk = 0;
-                if (st == ATA_OK && ata_plan_graph_kernels(e->plan, &nk) == ATA_OK) kernels += nk;
+                kernels += nk;
                 if (st == ATA_OK && cudaEventRecord(free_slot->done, free_slot->stream) != cudaSuccess) {
                     st = ATA_ECUDA;
                     emsg = "cudaEventRecord failed";

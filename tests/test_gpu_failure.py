@@ -106,6 +106,7 @@ def test_allocation_fault_in_host_staging(gpu):
         with pytest.raises(ata.AtaError) as e:
             ata.ata_execute_host(p, A_np, C_host)
         assert e.value.status == ata.ATA_ENOMEM
+        del e  # its traceback holds the plan
     finally:
         os.environ.pop("ATA_FAULT", None)
     ata.ata_execute_host(p, A_np, C_host)  # no injection: runs

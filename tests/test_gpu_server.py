@@ -4,7 +4,7 @@ ata_poll.  Each result must be bitwise equal to the same request run alone
 stated bound of the oracle.
 
 The server's streams do not wait for the caller's streams, so every input is
-complete (torch.cuda.synchronize) before it is submitted.  No test here
+complete (the current stream synchronised) before it is submitted.  No test here
 offers the server more work than it completes: plain-FP64 serving under
 overload is kept off the GPU (an unexplained illegal-address fault)."""
 import numpy as np
@@ -31,18 +31,21 @@ def test_mix_equals_alone_and_oracle(gpu, dtype):
         alone.append(p(A).clone())
     torch.cuda.synchronize()
     srv = ata.Server(8 << 30, dtype, max_inflight=4)
-    reqs = []
-    for rep in range(5):
-        for i, (m, n) in enumerate(shapes):
-            C = torch.full((n * (n + 1) // 2,), float("nan"), dtype=torch.float64, device="cuda")
-            torch.cuda.synchronize()  # the fill is done before the server's stream writes C
-            reqs.append((i, C, srv.submit(mats[i], C)))
-    for i, C, t in reqs:
-        assert srv.poll(t, 10_000_000) == ata.ATA_OK
-        assert torch.equal(C, alone[i])
-    st = srv.stats()
-    assert st["completed"] == len(reqs) and st["p99_us"] >= st["p50_us"] > 0
-    srv.close()
+    try:
+        reqs = []
+        for rep in range(5):
+            for i, (m, n) in enumerate(shapes):
+                C = torch.full((n * (n + 1) // 2,), float("nan"), dtype=torch.float64, device="cuda")
+                torch.cuda.current_stream().synchronize()  # the fill is done before the server writes C
+                reqs.append((i, C, srv.submit(mats[i], C)))
+        for i, C, t in reqs:
+            assert srv.poll(t, 10_000_000) == ata.ATA_OK
+            assert torch.equal(C, alone[i])
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["p99_us"] >= st["p50_us"] > 0
+        assert srv.kernels() > 0
+    finally:
+        srv.close()
     # every served result against the oracle (each request of a shape is
     # bitwise equal to the alone run, so one comparison per shape covers all)
     for i, a in enumerate(mats_np):
@@ -56,11 +59,13 @@ def test_budget_too_small_fails_the_request(gpu):
     A = torch.zeros((4096, 1024), dtype=torch.float32, device="cuda")
     C = torch.zeros(1024 * 1025 // 2, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
-    t = srv.submit(A, C)
-    with pytest.raises(ata.AtaError) as e:
-        srv.poll(t, 10_000_000)
-    assert e.value.status == ata.ATA_EBUSY
-    srv.close()
+    try:
+        t = srv.submit(A, C)
+        with pytest.raises(ata.AtaError) as e:
+            srv.poll(t, 10_000_000)
+        assert e.value.status == ata.ATA_EBUSY
+    finally:
+        srv.close()
 
 
 def test_poll_pending_and_unknown_ticket(gpu):
@@ -69,14 +74,16 @@ def test_poll_pending_and_unknown_ticket(gpu):
     A = torch.from_numpy(inputs.normal(4000, 2000, seed=1)).cuda()
     C = torch.empty(2000 * 2001 // 2, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
-    t = srv.submit(A, C)
-    st = srv.poll(t, 0)
-    assert st in (ata.ATA_OK, ata.ATA_PENDING)
-    if st == ata.ATA_PENDING:
-        assert srv.poll(t, 30_000_000) == ata.ATA_OK
-    with pytest.raises(ata.AtaError):
-        srv.poll(t + 1000, 0)
-    srv.close()
+    try:
+        t = srv.submit(A, C)
+        st = srv.poll(t, 0)
+        assert st in (ata.ATA_OK, ata.ATA_PENDING)
+        if st == ata.ATA_PENDING:
+            assert srv.poll(t, 30_000_000) == ata.ATA_OK
+        with pytest.raises(ata.AtaError):
+            srv.poll(t + 1000, 0)
+    finally:
+        srv.close()
 
 
 def test_poll_times_out_then_completes(gpu):
@@ -91,10 +98,12 @@ def test_poll_times_out_then_completes(gpu):
     C = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     srv = ata.Server(8 << 30, ata.ATA_F64, max_inflight=1)
-    t = srv.submit(A, C)
-    assert srv.poll(t, 200) == ata.ATA_ETIMEOUT
-    assert srv.poll(t, 60_000_000) == ata.ATA_OK
-    srv.close()
+    try:
+        t = srv.submit(A, C)
+        assert srv.poll(t, 200) == ata.ATA_ETIMEOUT
+        assert srv.poll(t, 60_000_000) == ata.ATA_OK
+    finally:
+        srv.close()
     I = np.arange(0, n, 97)
     J = np.minimum(I + 5, n - 1)
     got = C[torch.from_numpy(oracle.packed_index(I, J, n)).cuda()].cpu().numpy()

@@ -412,7 +412,18 @@ def run_ours(args):
     if args.cutoff is not None:
         cutoff = args.cutoff
     A_np = make_input(name)
-    plan = ata.Plan(m, n, MODE_CODES[mode], cutoff)
+    tuning = None
+    if cutoff == 0 and not args.model_cutoff:
+        # the cutoff and tile form measured on this device (ata_tune), before
+        # the timed region
+        t0 = time.perf_counter()
+        opts = ata.ata_tune(m, n, MODE_CODES[mode], candidates=3)
+        tuning = {"measured_ms": opts.pop("best_ms"), "tuning_s": time.perf_counter() - t0,
+                  "how": "ata_tune: the cost model's 3 best cutoffs x (single-CTA, CTA-pair) tiles timed on "
+                         "this GPU, median of 3"}
+        plan = ata.Plan(m, n, MODE_CODES[mode], **opts)
+    else:
+        plan = ata.Plan(m, n, MODE_CODES[mode], cutoff)
     info = plan.info
     A = torch.from_numpy(A_np).to(dev)
     C = torch.empty(n * (n + 1) // 2, dtype=torch.float64, device=dev)
@@ -516,7 +527,7 @@ def run_ours(args):
                   "tf32": "tf32"}[mode], "data": "synthetic",
         "config": workload_config(name, world, A_np.nbytes, cutoff),
         "plan": {"cutoff": info["cutoff"], "strassen_levels_max": info["max_strassen_levels"],
-                 "leaf_tile": [info["leaf_tile_rows"], info["leaf_tile_cols"]]},
+                 "leaf_tile": [info["leaf_tile_rows"], info["leaf_tile_cols"]], "tuning": tuning},
         "error": {err_kind + "_sampled": err, "tolerance": tol, "samples": cnt, "device_status": dev_status},
         "stages_ms": {"split": statistics.mean(split_ms), "prep": statistics.mean(prep_ms),
                       "leaf": statistics.mean(leaf_ms), "combine": statistics.mean(comb_ms)},
@@ -597,8 +608,53 @@ def run_batched(args, mode):
     torch.cuda.set_device(dev)
     dt = np.float64 if mode in ("f64", "ozaki") else np.float32
     mats = [a.astype(dt) for a in inputs.batch(512, seed=3)]
-    plans = [ata.Plan(a.shape[0], a.shape[1], MODE_CODES[mode], 0) for a in mats]
-    batch = ata.Batch(plans)
+    tuning = None
+
+    def make_batch(policy):
+        cut = (lambda a: 0) if policy == "model" else (lambda a: int(policy))
+        ps = [ata.Plan(a.shape[0], a.shape[1], MODE_CODES[mode], cut(a)) for a in mats]
+        return ps, ata.Batch(ps)
+
+    if args.model_cutoff:
+        plans, batch = make_batch("model")
+    else:
+        # The cutoff policy measured on this device for the whole batch
+        # (before the timed region): the planner's cost model per shape, or
+        # one cutoff for every instance.  Each candidate batch runs once
+        # untimed and three times timed; the fastest median wins.  (Timing
+        # each shape alone misleads here: a small instance alone is timed
+        # mostly on its launch latency, which the merged batch does not pay;
+        # per-bucket choices made that way ran 5% slower.)
+        t0 = time.perf_counter()
+        hA = torch.zeros(1, dtype=torch.float32)
+        times = {}
+        best = None
+        for policy in ["model", 4096, 1024, 512]:
+            ps, b = make_batch(policy)
+            hA = torch.zeros(b.a_numel, dtype=b.in_dtype)
+            for v, a in zip(b.input_views(hA), mats):
+                v.copy_(torch.from_numpy(a))
+            dA = hA.to(dev)
+            dC = torch.empty(b.c_numel, dtype=torch.float64, device=dev)
+            b(dA, dC)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(3):
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                b(dA, dC)
+                s1.record()
+                torch.cuda.synchronize()
+                ts.append(s0.elapsed_time(s1))
+            times[str(policy)] = float(np.median(ts))
+            if best is None or times[str(policy)] < times[str(best)]:
+                best = policy
+            del ps, b, dA, dC
+            torch.cuda.empty_cache()
+        plans, batch = make_batch(best)
+        tuning = {"chosen": str(best), "measured_ms": times, "tuning_s": time.perf_counter() - t0,
+                  "how": "whole batch timed on this GPU under each cutoff policy (cost model per shape, or one "
+                         "cutoff for all), median of 3"}
     # the packed input in pinned host memory, and its device copy
     hostA = torch.zeros(batch.a_numel, dtype=batch.in_dtype).pin_memory()
     for v, a in zip(batch.input_views(hostA), mats):
@@ -670,7 +726,7 @@ def run_batched(args, mode):
     line = _line_common(args, world, "effective TFLOP/s (m*n^2 FMAs) of C = A^t A, 512 batched instances",
                         world * eff / (ms / 1e3) / 1e12, "TFLOP/s", ms, mode,
                         {"workload": f"batched_{mode}", "instances": 512, "m_range": [64, 4096],
-                         "n_range": [32, 1024], "generator": "uniform(-1,1) seed 3", "cutoff": "autotuned per shape",
+                         "n_range": [32, 1024], "generator": "uniform(-1,1) seed 3", "cutoff": "cost model per shape" if args.model_cutoff else "policy measured on the batch",
                          "parallelism": f"replicas{world}", "calls": "one ata_batch_execute per step",
                          "l2": "inputs larger than L2 (%.0f MB)" % (sum(a.nbytes for a in mats) / 2**20)})
     line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -684,6 +740,7 @@ def run_batched(args, mode):
     line["error"] = {kind + "_max_of_16": max(errs), "tolerance": tol,
                      "checked": "every 64th instance, device-timed and end-to-end results"}
     line["clocks"] = clocks
+    line["tuning"] = tuning
     return line if rank == 0 else None
 
 
@@ -1070,6 +1127,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cutoff", type=int, default=None, help="override the workload's cutoff")
+    ap.add_argument("--model-cutoff", action="store_true",
+                    help="take the planner's cost-model cutoff instead of measuring candidates (ata_tune)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

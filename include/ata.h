@@ -224,6 +224,24 @@ ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype,
                                const ata_plan_options* opts,
                                ata_plan_info* out);
 
+/* Measured tuning: chooses the cutoff (and, when base->cta_pair is -1 in a
+ * tensor-core mode, single-CTA or CTA-pair tiles) for an m x n product by
+ * timing on the current device.  The planner's cost model ranks the
+ * cutoffs; its best `candidates` (1..8), each with both tile forms where
+ * they are tuned, run on a synthetic input of the exact shape (device
+ * buffers allocated and freed here): one untimed execution, then three
+ * timed with CUDA events on a stream of the call's own; the median decides.
+ * Fills *out with base's options and the winning cutoff and cta_pair, and
+ * *best_ms (may be NULL) with the winner's median time.  Results are cached
+ * per (m, n, dtype, base options) for the process, so a second call returns
+ * at once.  base may be NULL (all defaults; its cutoff is ignored).  Runs
+ * work on the device and synchronises with it: call it before the timed or
+ * captured part of an application.
+ * Errors: as ata_plan_query_opts, ATA_ENOMEM (no candidate fits), ATA_ECUDA. */
+ata_status ata_tune(int64_t m, int64_t n, ata_dtype dtype,
+                    const ata_plan_options* base, int candidates,
+                    ata_plan_options* out, float* best_ms);
+
 /* Statistics of a created plan. */
 ata_status ata_plan_get_info(ata_plan plan, ata_plan_info* out);
 

@@ -20,7 +20,7 @@ __all__ = [
     "AtaError", "Plan", "Server", "ata_plan_query", "ata_plan_create", "ata_execute", "ata_execute_host",
     "ata_execute_host_async", "ata_plan_wait", "ata_batched_graph_kernels",
     "ata_execute_batched", "Batch", "packed_layout", "ata_plan_destroy", "ata_server_create", "ata_submit", "ata_poll", "load",
-    "packed_size", "lib_path", "ata_device_bytes_held",
+    "packed_size", "lib_path", "ata_device_bytes_held", "ata_tune",
 ]
 
 ATA_F64, ATA_F32_BF16X3, ATA_F32_TF32, ATA_F64_OZAKI = 0, 1, 2, 3
@@ -88,6 +88,8 @@ def load():
         "ata_gemm_plan_create": ([ctypes.POINTER(vp), i64, i64, i64, i32, ctypes.POINTER(PlanOptions)], i32),
         "ata_gemm_tn": ([vp, vp, i64, vp, i64, dp, i64, vp], i32),
         "ata_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i32),
+        "ata_tune": ([i64, i64, i32, ctypes.POINTER(PlanOptions), i32, ctypes.POINTER(PlanOptions),
+                      ctypes.POINTER(ctypes.c_float)], i32),
         "ata_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], i32),
         "ata_execute": ([vp, vp, i64, dp, vp], i32),
         "ata_execute_host": ([vp, vp, i64, dp, vp], i32),
@@ -157,6 +159,20 @@ def ata_plan_query(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts) -> di
     o = _opts(cutoff, **opts)
     _check(load().ata_plan_query_opts(m, n, _dtype_code(dtype), ctypes.byref(o), ctypes.byref(info)))
     return info.as_dict()
+
+
+def ata_tune(m: int, n: int, dtype=ATA_F64, candidates: int = 3, **opts) -> dict:
+    """Measured tuning on the current device (``ata_tune``): returns the
+    winning plan options as keyword arguments for :class:`Plan` (``cutoff``,
+    ``cta_pair`` and the given ones) and ``best_ms``."""
+    base = _opts(0, **opts)
+    out = PlanOptions()
+    ms = ctypes.c_float()
+    _check(load().ata_tune(int(m), int(n), _dtype_code(dtype), ctypes.byref(base), int(candidates),
+                           ctypes.byref(out), ctypes.byref(ms)))
+    res = {k: getattr(out, k) for k, _ in PlanOptions._fields_}
+    res["best_ms"] = ms.value
+    return res
 
 
 def ata_plan_check(m: int, n: int, dtype=ATA_F64, cutoff: int = 0, **opts):

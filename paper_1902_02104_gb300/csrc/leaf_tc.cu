@@ -45,6 +45,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <queue>
 #include <set>
 #include <tuple>
 #include <vector>
@@ -1058,7 +1059,8 @@ __global__ void __launch_bounds__(256) tc_prep_fixed_kernel(const __grid_constan
 template <int NB, int MODE, int CG>
 __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ BindSet<NB> bs, const TcProd* __restrict__ tcp,
-                   const LeafTile* __restrict__ tiles, int ntiles, int* __restrict__ status, uint64_t wait_ns) {
+                   const LeafTile* __restrict__ sched, const int32_t* __restrict__ wfirst,
+                   int* __restrict__ status, uint64_t wait_ns) {
     using G = Geo<MODE>;
     using SH = Shape<MODE, CG, NB>;
     constexpr int NSTAGE = SH::NSTAGE;
@@ -1089,8 +1091,9 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = CG == 1 ? 0u : cluster_rank();
-    const int tile0 = CG == 1 ? (int)blockIdx.x : (int)cluster_index();
-    const int tstep = CG == 1 ? (int)gridDim.x : (int)cluster_count();
+    // this worker's tiles (a CTA, or a CTA pair): sched[t_beg .. t_end)
+    const int worker = CG == 1 ? (int)blockIdx.x : (int)cluster_index();
+    const int t_beg = __ldg(wfirst + worker), t_end = __ldg(wfirst + worker + 1);
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(b_full + 8 * s, 1);
@@ -1127,8 +1130,8 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = tile0; t < ntiles && ok; t += tstep) {
-                const LeafTile lt = tiles[t];
+            for (int t = t_beg; t < t_end && ok; ++t) {
+                const LeafTile lt = sched[t];
                 const TcProd* pr = tcp + lt.prod;
                 const int nkb = pr->K_pad / G::KBLK;
                 const int ya = lt.ti * (128 * CG) + (int)rank * SH::XROWS;
@@ -1183,8 +1186,8 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
             // shared-memory address), so each is one add of a constant.
             const uint64_t desc_a0 = make_desc(smem_base, G::SBO, G::SWZ);
             const uint64_t desc_b0 = make_desc(smem_base + G::PARTS * SH::X_BYTES, G::SBO, G::SWZ);
-            for (int t = tile0; t < ntiles && ok; t += tstep) {
-                const LeafTile lt = tiles[t];
+            for (int t = t_beg; t < t_end && ok; ++t) {
+                const LeafTile lt = sched[t];
                 const int nkb = tcp[lt.prod].K_pad / G::KBLK;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const StageFlags fl = stage_flags<kbpc, FOFF, FKC>(kb, nkb);
@@ -1293,8 +1296,8 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
         if (rank == 0) {
             uint32_t it = 0, chunk = 0, fchunk = 0, tcount = 0;
             bool ok = true;
-            for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
-                const LeafTile lt = tiles[t];
+            for (int t = t_beg; t < t_end && ok; ++t, ++tcount) {
+                const LeafTile lt = sched[t];
                 const int nkb = tcp[lt.prod].K_pad / G::KBLK;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const StageFlags fl = stage_flags<kbpc, FOFF, FKC>(kb, nkb);
@@ -1343,8 +1346,8 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
         const int row = 32 * q + lane;
         uint32_t chunk = 0, fchunk = 0, tcount = 0;
         bool ok = true;
-        for (int t = tile0; t < ntiles && ok; t += tstep, ++tcount) {
-            const LeafTile lt = tiles[t];
+        for (int t = t_beg; t < t_end && ok; ++t, ++tcount) {
+            const LeafTile lt = sched[t];
             const TcProd* pr = tcp + lt.prod;
             const int nkb = pr->K_pad / G::KBLK;
             float hi[NCOL];
@@ -1657,7 +1660,7 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
         if (t.tc_pair) {
             using SH = Shape<MODE, 2>;
             if (g_pair_clusters[MODE] < 1) return cudaErrorInvalidConfiguration;
-            const int nclus = std::max(1, std::min(t.ntiles, g_pair_clusters[MODE]));
+            const int nclus = std::max(1, t.nworkers);
             cudaLaunchAttribute at[1] = {pair_cluster_attr()};
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(2 * nclus);
@@ -1666,13 +1669,13 @@ cudaError_t launch_mode(const DeviceTables& t, const BindSet<NB>& bs, cudaStream
             cfg.stream = s;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, MODE, 2>, bs, t.tcp, t.tiles, t.ntiles, t.status,
+            return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, MODE, 2>, bs, t.tcp, t.sched, t.wfirst, t.status,
                                       wait_limit(t));
         }
     }
     using SH = Shape<MODE, 1, NB>;
-    const int grid = std::max(1, std::min(t.ntiles, g_sms));
-    tc_gemm_kernel<NB, MODE, 1><<<grid, SH::THREADS, SH::SMEM, s>>>(bs, t.tcp, t.tiles, t.ntiles, t.status,
+    const int grid = std::max(1, t.nworkers);
+    tc_gemm_kernel<NB, MODE, 1><<<grid, SH::THREADS, SH::SMEM, s>>>(bs, t.tcp, t.sched, t.wfirst, t.status,
                                                                      wait_limit(t));
     return cudaGetLastError();
 }
@@ -1756,9 +1759,66 @@ int tc_rows_for(const Plan& P) {
     return g_pair_clusters[P.leaf] > 0 ? kTcPairRows : kTcTile;
 }
 
+namespace {
+
+// Leaf tile schedule.  Each worker of the persistent leaf launch (a CTA, or a
+// CTA pair) runs its own contiguous list of tiles.  Tiles are taken longest
+// first and each goes to the worker with the least work so far (ties to the
+// lowest worker), the longest-processing-time rule; a tile's cost is its
+// K-blocks plus a fixed cost per tile for its first loads, its last drain and
+// its output (about 5000 clocks, in K-blocks of the mode).  Tiles of equal
+// cost are dealt round robin, in their table order (heaviest products
+// first).  Short and uneven tiles (batched instances) no longer leave a
+// tail of workers that were dealt more of them than the others.
+void leaf_schedule(const HostTables& h, int nw, std::vector<LeafTile>* sched, std::vector<int32_t>* wfirst) {
+    const int ntiles = (int)h.tiles.size();
+    int kblk = Geo<MODE_BF16X3>::KBLK, over = 4;
+    if (h.leaf == LEAF_TF32) {
+        kblk = Geo<MODE_TF32>::KBLK;
+        over = 10;
+    } else if (h.leaf == LEAF_OZAKI) {
+        kblk = Geo<MODE_OZAKI>::KBLK;
+        over = 3;
+    }
+    std::vector<int64_t> cost(ntiles);
+    std::vector<int> idx(ntiles);
+    for (int i = 0; i < ntiles; ++i) {
+        cost[i] = h.prods[h.tiles[i].prod].K_pad / kblk + over;
+        idx[i] = i;
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<int64_t, int>;  // (work so far, worker)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int w = 0; w < nw; ++w) heap.push({0, w});
+    std::vector<std::vector<int>> lists(nw);
+    for (int i : idx) {
+        Load l = heap.top();
+        heap.pop();
+        lists[l.second].push_back(i);
+        l.first += cost[i];
+        heap.push(l);
+    }
+    sched->clear();
+    wfirst->assign(nw + 1, 0);
+    for (int w = 0; w < nw; ++w) {
+        (*wfirst)[w] = (int32_t)sched->size();
+        for (int i : lists[w]) sched->push_back(h.tiles[i]);
+    }
+    (*wfirst)[nw] = (int32_t)sched->size();
+}
+
+}  // namespace
+
 ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, DeviceTables* d) {
     ata_status st = tc_prepare_device();
     if (st != ATA_OK) return st;
+    // workers of the leaf launch: CTAs (one per SM) or CTA pairs
+    const int ntiles_all = (int)h.tiles.size();
+    const int wmax = h.tile_rows == kTcPairRows ? g_pair_clusters[h.leaf] : g_sms;
+    const int nw = std::max(1, std::min(ntiles_all, std::max(1, wmax)));
+    std::vector<LeafTile> sched;
+    std::vector<int32_t> wfirst;
+    leaf_schedule(h, nw, &sched, &wfirst);
     const int np = (int)h.prods.size();
     std::vector<TcProd> tp(np);
     std::vector<PrepTask> prep, colmax;
@@ -1975,7 +2035,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     const int64_t o_scale = al(o_amx + (int64_t)atom_mx.size() * 8);
     const int64_t o_cole = al(o_scale + (int64_t)scale.size() * sizeof(PrepTask));
     const int64_t o_status = al(o_cole + (h.leaf == LEAF_OZAKI ? ex_elems * 4 : 0));
-    const int64_t o_ex = al(o_status + 256);
+    const int64_t o_sched = al(o_status + 256);
+    const int64_t o_wfirst = al(o_sched + (int64_t)sched.size() * sizeof(LeafTile));
+    const int64_t o_ex = al(o_wfirst + (int64_t)wfirst.size() * 4);
     const int64_t ex_total = std::max<int64_t>(ex_elems + tm_elems, 1);
     const int64_t total = al(o_ex + ex_total * 8);
     char* blob = nullptr;
@@ -1997,6 +2059,8 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
         std::memcpy(hb.data() + o_aterm, atom_terms.data(), atom_terms.size() * sizeof(Term));
     if (!atom_mx.empty()) std::memcpy(hb.data() + o_amx, atom_mx.data(), atom_mx.size() * 8);
     if (!scale.empty()) std::memcpy(hb.data() + o_scale, scale.data(), scale.size() * sizeof(PrepTask));
+    if (!sched.empty()) std::memcpy(hb.data() + o_sched, sched.data(), sched.size() * sizeof(LeafTile));
+    std::memcpy(hb.data() + o_wfirst, wfirst.data(), wfirst.size() * 4);
     cudaError_t e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         dev_free(blob);
@@ -2019,6 +2083,9 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
     d->term_max = reinterpret_cast<unsigned long long*>(blob + o_ex) + ex_elems;
     d->tc_ex = blob + o_ex;
     d->tc_ex_bytes = (size_t)ex_total * 8;
+    d->sched = reinterpret_cast<LeafTile*>(blob + o_sched);
+    d->wfirst = reinterpret_cast<int32_t*>(blob + o_wfirst);
+    d->nworkers = nw;
     return ATA_OK;
 }
 

@@ -94,9 +94,14 @@ void dev_free(void* p) {
 
 static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Row chunks of an elementwise task (split or combine), one block each: about
+// 2048 elements (8 per thread of a 256-thread block), so that a level's
+// launch has several blocks per SM even when it holds a single Strassen node
+// (a 1125 x 1125 combine: 563 blocks; with 16384-element chunks it had 75
+// and reached 8% of HBM bandwidth).
 void build_chunks(int64_t rows, int64_t cols, int32_t task, std::vector<Chunk>* out) {
     if (rows <= 0 || cols <= 0) return;
-    const int64_t per = std::max<int64_t>(1, (16384 + cols - 1) / cols);
+    const int64_t per = std::max<int64_t>(1, (2048 + cols - 1) / cols);
     for (int64_t r0 = 0; r0 < rows; r0 += per) {
         Chunk c;
         c.task = task;
@@ -275,6 +280,9 @@ void DeviceTables::free_all() {
     atom_terms = nullptr;
     term_max = nullptr;
     status = nullptr;
+    sched = nullptr;
+    wfirst = nullptr;
+    nworkers = 0;
 }
 
 // Queues one execution of `t` with bindings `binds` on `s` (no graph).

@@ -95,6 +95,10 @@ struct DeviceTables {
     char* tc_ex = nullptr;     // FP64 emulation: column maxima (zeroed per run)
     size_t tc_ex_bytes = 0;
     uint64_t wait_ns = 0;      // limit of the leaf kernel's pipeline waits (0 = its default)
+    // leaf tile schedule: worker w (a CTA or a CTA pair) runs sched[wfirst[w] .. wfirst[w+1])
+    LeafTile* sched = nullptr;
+    int32_t* wfirst = nullptr;
+    int nworkers = 0;
     void free_all();
 };
 
@@ -160,6 +164,9 @@ int default_cutoff(int64_t m, int64_t n, ata_dtype dtype);
 int default_fuse_levels(ata_dtype dtype, int variant);
 // r >= 0 tunes the general product X^t Y (X: m x n, Y: m x r) instead.
 ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o, int64_t r = -1);
+// The cost model's cutoff candidates for plan options o, fastest first.
+std::vector<std::pair<double, int>> rank_cutoffs(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
+                                                 int64_t r);
 
 // Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
 const Plan& plan_of(ata_plan p);

@@ -136,6 +136,31 @@ int default_cutoff(int64_t m, int64_t n, ata_dtype dtype) {
     }
 }
 
+// Cutoff candidates ranked by the cost model (fastest first).
+std::vector<std::pair<double, int>> rank_cutoffs(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
+                                                 int64_t r) {
+    static const int cands[] = {64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    std::vector<std::pair<double, int>> out;
+    for (int c : cands) {
+        if (r < 0 && estimate_products(m, n, c) > kMaxLeafProducts) continue;
+        if (dtype != ATA_F64 && c < 256) continue;  // tensor-core tiles are 128 x 128
+        PlanOptions t = o;
+        t.cutoff = c;
+        Plan P;
+        std::string err;
+        if (!(r < 0 ? build_plan(m, n, t, &P, &err) : build_gemm_plan(m, n, r, t, &P, &err))) continue;
+        if ((int64_t)P.products.size() > kMaxLeafProducts) continue;
+        if (P.ws_bytes > kWorkspaceCap) continue;
+        bool terms_ok = true;
+        for (const LeafProduct& lp : P.products) terms_ok = terms_ok && lp.nx <= kMaxTerms && lp.ny <= kMaxTerms;
+        if (!terms_ok) continue;
+        out.push_back({model_time(P, dtype), c});
+    }
+    std::stable_sort(out.begin(), out.end(),
+                     [](const std::pair<double, int>& a, const std::pair<double, int>& b) { return a.first < b.first; });
+    return out;
+}
+
 ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o, int64_t r) {
     const auto key = std::make_tuple(m, n, r, (int)dtype, variant, o->fuse_levels, o->max_levels, (int)o->cta_pair);
     {
@@ -146,28 +171,8 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
             return ATA_OK;
         }
     }
-    static const int cands[] = {64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
-    double best = 1e300;
-    int best_c = o->cutoff;
-    for (int c : cands) {
-        if (r < 0 && estimate_products(m, n, c) > kMaxLeafProducts) continue;
-        if (dtype != ATA_F64 && c < 256) continue;  // tensor-core tiles are 128 x 128
-        PlanOptions t = *o;
-        t.cutoff = c;
-        Plan P;
-        std::string err;
-        if (!(r < 0 ? build_plan(m, n, t, &P, &err) : build_gemm_plan(m, n, r, t, &P, &err))) continue;
-        if ((int64_t)P.products.size() > kMaxLeafProducts) continue;
-        if (P.ws_bytes > kWorkspaceCap) continue;
-        bool terms_ok = true;
-        for (const LeafProduct& lp : P.products) terms_ok = terms_ok && lp.nx <= kMaxTerms && lp.ny <= kMaxTerms;
-        if (!terms_ok) continue;
-        const double tm = model_time(P, dtype);
-        if (tm < best) {
-            best = tm;
-            best_c = c;
-        }
-    }
+    const auto ranked = rank_cutoffs(m, n, dtype, *o, r);
+    const int best_c = ranked.empty() ? o->cutoff : ranked.front().second;
     o->cutoff = best_c;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best_c;
@@ -175,3 +180,168 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
 }
 
 }  // namespace ata
+
+// ---------------------------------------------------------------------------
+// Measured tuning (ata_tune): the cost model ranks the cutoffs; the best few,
+// and single-CTA against CTA-pair tiles in the tensor-core modes, are timed
+// on this device with CUDA events on a synthetic input of the exact shape,
+// and the fastest wins.  Results are cached per (shape, dtype, options).
+
+namespace ata {
+namespace {
+
+// Deterministic fill of the tuning input: values in [-1, 1) from a 64-bit
+// integer hash of the index (timing does not depend on them, but they
+// exercise every slice and every column scale).
+__global__ void tune_fill_kernel(void* A, int64_t count, int f64) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull;
+        h ^= h >> 31;
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 29;
+        const double v = (double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+        if (f64)
+            static_cast<double*>(A)[i] = v;
+        else
+            static_cast<float*>(A)[i] = (float)v;
+    }
+}
+
+struct TuneKey {
+    int64_t m, n;
+    int dtype, variant, fuse, max_levels, cta_pair;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(m, n, dtype, variant, fuse, max_levels, cta_pair) <
+               std::tie(o.m, o.n, o.dtype, o.variant, o.fuse, o.max_levels, o.cta_pair);
+    }
+};
+std::map<TuneKey, std::pair<ata_plan_options, float>> g_measured;
+
+}  // namespace
+}  // namespace ata
+
+extern "C" ata_status ata_tune(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* base, int candidates,
+                               ata_plan_options* out, float* best_ms) {
+    using namespace ata;
+    if (!out) return fail(ATA_EINVAL, "out is NULL");
+    if (candidates < 1 || candidates > 8) return fail(ATA_EINVAL, "candidates must be in [1, 8]");
+    ata_plan_options u;
+    if (base) {
+        u = *base;
+    } else {
+        u.cutoff = 0;
+        u.variant = -1;
+        u.fuse_levels = -1;
+        u.max_strassen_levels = -1;
+        u.cta_pair = -1;
+        u.wait_limit_us = -1;
+    }
+    u.cutoff = 0;
+    const bool tune_pair = u.cta_pair < 0;
+    ata_plan_info info;
+    ata_status st = ata_plan_query_opts(m, n, dtype, &u, &info);  // validates the arguments
+    if (st != ATA_OK) return st;
+    const TuneKey key{m, n, (int)dtype, u.variant, u.fuse_levels, u.max_strassen_levels, u.cta_pair};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_measured.find(key);
+        if (it != g_measured.end()) {
+            *out = it->second.first;
+            if (best_ms) *best_ms = it->second.second;
+            return ATA_OK;
+        }
+    }
+    // candidate cutoffs: the model's best `candidates` (with the options as
+    // the plan would resolve them)
+    PlanOptions o;
+    o.leaf = dtype == ATA_F64 ? LEAF_F64 : dtype == ATA_F32_BF16X3 ? LEAF_BF16X3 : dtype == ATA_F32_TF32 ? LEAF_TF32 : LEAF_OZAKI;
+    o.variant = u.variant < 0 ? ATA_STRASSEN : u.variant;
+    o.fuse_levels = u.fuse_levels >= 0 ? u.fuse_levels : default_fuse_levels(dtype, o.variant);
+    o.max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : 64;
+    o.cta_pair = u.cta_pair == 1 || (u.cta_pair < 0 && dtype == ATA_F32_TF32);
+    auto ranked = rank_cutoffs(m, n, dtype, o, -1);
+    if (ranked.empty()) ranked.push_back({0.0, info.cutoff});
+    if ((int)ranked.size() > candidates) ranked.resize(candidates);
+    std::vector<ata_plan_options> cands;
+    for (const auto& rc : ranked) {
+        ata_plan_options c = u;
+        c.cutoff = rc.second;
+        if (dtype == ATA_F64 || !tune_pair) {
+            cands.push_back(c);
+        } else {
+            c.cta_pair = 0;
+            cands.push_back(c);
+            c.cta_pair = 1;
+            cands.push_back(c);
+        }
+    }
+    // synthetic input of the exact shape and an output buffer
+    const int es = (dtype == ATA_F64 || dtype == ATA_F64_OZAKI) ? 8 : 4;
+    void* A = nullptr;
+    double* C = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (s) cudaStreamSynchronize(s);
+        dev_free(A);
+        dev_free(C);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    };
+    const int64_t a_elems = std::max<int64_t>(m * n, 1), c_elems = std::max<int64_t>(n * (n + 1) / 2, 1);
+    if (dev_malloc(&A, (size_t)a_elems * es) != cudaSuccess || dev_malloc(&C, (size_t)c_elems * 8) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(ATA_ENOMEM, "tuning buffers");
+    }
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return cuda_fail(cudaGetLastError(), "tuning stream/events");
+    }
+    tune_fill_kernel<<<1024, 256, 0, s>>>(A, a_elems, es == 8);
+    float best = 1e30f;
+    ata_plan_options best_o = cands.front();
+    st = ATA_OK;
+    for (const ata_plan_options& c : cands) {
+        ata_plan p = nullptr;
+        ata_status cs = ata_plan_create_opts(&p, m, n, dtype, &c);
+        if (cs == ATA_ENOMEM) continue;  // a candidate that does not fit is skipped
+        if (cs != ATA_OK) {
+            st = cs;
+            break;
+        }
+        float times[3];
+        for (int rep = 0; rep < 4 && cs == ATA_OK; ++rep) {
+            if (rep > 0 && cudaEventRecord(e0, s) != cudaSuccess) cs = ATA_ECUDA;
+            if (cs == ATA_OK) cs = ata_execute(p, A, n, C, s);
+            if (cs == ATA_OK && rep > 0) {
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&times[rep - 1], e0, e1) != cudaSuccess)
+                    cs = ATA_ECUDA;
+            }
+        }
+        ata_plan_destroy(p);
+        if (cs != ATA_OK) {
+            st = cs;
+            break;
+        }
+        std::sort(times, times + 3);
+        if (times[1] < best) {
+            best = times[1];
+            best_o = c;
+        }
+    }
+    cleanup();
+    if (st != ATA_OK) return st;
+    if (best >= 1e30f) return fail(ATA_ENOMEM, "no tuning candidate fits on the device");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_measured[key] = {best_o, best};
+    }
+    *out = best_o;
+    if (best_ms) *best_ms = best;
+    return ATA_OK;
+}

@@ -98,10 +98,13 @@ def tensor_peak(mode):
     return bf16, f"{src} bf16 (burst)"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the leaf kernel on the full-size workload, from a one-pass ncu capture
-# (profiles/), valid only for the kernel source it was taken on (the first 16
-# hex digits of the sha256 of leaf_tc.cu or kernels_f64.cu).
+# the leaf kernel on the full-size workload, from ncu captures, valid only for
+# the kernel source it was taken on (the first 16 hex digits of the sha256 of
+# leaf_tc.cu or kernels_f64.cu).
 LEAF_TRAFFIC = {
+    # a one-launch capture of the 4500^2 small case (cutoff 1200), scaled by
+    # the ratio of tree multiplications (traffic grows with tiles x K)
+    ("ata_ozaki_10000x10000", "8055985539fd8bb4"): (940.1e6 + 96.1e6) * 468800000000 / 42724968750,
     ("ata_ozaki_10000x10000", "e3737c832598ccb7"): 10.945e9 + 0.571e9,
     ("ata_bf16x3_16384x8192", "e3737c832598ccb7"): 5.973e9 + 0.270e9,
     ("ata_tf32_16384x8192", "e3737c832598ccb7"): 2.412e9 + 0.245e9,

@@ -139,6 +139,7 @@ void forget_plan_in_batches(uint64_t id) {
 
 extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, const void* const* A, const int64_t* lda,
                                           double* const* C_packed, void* stream) {
+    NvtxRange nv("ata_execute_batched");
     if (count < 0) return fail(ATA_EINVAL, "count must be >= 0");
     if (count == 0) return ATA_OK;
     if (!plans || !A || !lda || !C_packed) return fail(ATA_EINVAL, "NULL array argument");
@@ -219,6 +220,7 @@ extern "C" ata_status ata_batch_create(ata_batch* out, const ata_plan* plans, in
 }
 
 extern "C" ata_status ata_batch_execute(ata_batch b, const void* A, double* C, void* stream) {
+    NvtxRange nv("ata_batch_execute");
     if (!b) return fail(ATA_EINVAL, "NULL batch");
     const int count = (int)b->plans.size();
     if (count == 0) return ATA_OK;

@@ -523,6 +523,10 @@ struct ata_plan_s {
     GraphCache graph;
     std::mutex mu;
     int64_t check = 0;          // self-checked kernels (ATA_CHECK_BOUNDS=1 at creation)
+    // canary guard bands around the workspace (ATA_CANARY=1 at creation):
+    // ws_base = ws - guard; guard bytes of kCanaryByte before and after
+    char* ws_base = nullptr;
+    int64_t guard = 0;
     uint64_t wait_ns = 0;       // tensor-core leaves: pipeline wait limit (0 = default)
     // staging for ata_execute_host
     void* stage_A = nullptr;
@@ -532,7 +536,7 @@ struct ata_plan_s {
         pipe.release();
         graph.release();
         tables.free_all();
-        dev_free(ws);
+        dev_free(ws_base ? ws_base : ws);
         dev_free(stage_A);
         dev_free(stage_C);
     }
@@ -695,6 +699,7 @@ ata_status execute_on(ata_plan plan, const void* A, int64_t lda, double* C_packe
 // results are the same bits.  Returns the number of kernels launched.
 ata_status ata::execute_direct(ata_plan plan, const void* A, int64_t lda, double* C_packed, cudaStream_t s,
                                int* kernels) {
+    NvtxRange nv("ata_server: execute");
     *kernels = 0;
     if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan");
     const int64_t n = plan->plan.n;
@@ -911,6 +916,9 @@ ata_status resolve_options(int64_t m, int64_t n, int64_t r, ata_dtype dtype, con
 }
 
 // Allocates the workspace and tables of a built plan.
+constexpr int64_t kCanaryBytes = 65536;  // keeps the workspace 256-byte aligned
+constexpr int kCanaryByte = 0xA5;
+
 ata_status finish_create(std::unique_ptr<ata_plan_s>& p, ata_dtype dtype) {
     ata_status st = check_terms(p->plan);
     if (st != ATA_OK) return st;
@@ -922,11 +930,19 @@ ata_status finish_create(std::unique_ptr<ata_plan_s>& p, ata_dtype dtype) {
         p->check = (chk && chk[0] == '1') ? 1 : 0;
     }
     ATA_CUDA(cudaGetDevice(&p->device));
+    {
+        const char* cn = getenv("ATA_CANARY");
+        p->guard = (cn && cn[0] == '1' && p->plan.ws_bytes > 0) ? kCanaryBytes : 0;
+    }
     if (p->plan.ws_bytes > 0) {
-        cudaError_t e = dev_malloc(&p->ws, p->plan.ws_bytes);
+        cudaError_t e = dev_malloc(&p->ws_base, p->plan.ws_bytes + 2 * p->guard);
+        if (e == cudaSuccess && p->guard > 0) {
+            e = cudaMemset(p->ws_base, kCanaryByte, p->guard);
+            if (e == cudaSuccess) e = cudaMemset(p->ws_base + p->guard + p->plan.ws_bytes, kCanaryByte, p->guard);
+        }
+        p->ws = p->ws_base ? p->ws_base + p->guard : nullptr;
         if (e != cudaSuccess) {
             cudaGetLastError();
-            p->ws = nullptr;
             return fail(ATA_ENOMEM, "workspace: cudaMalloc of " + std::to_string(p->plan.ws_bytes) + " bytes failed");
         }
     }
@@ -975,6 +991,7 @@ ata_status ata_gemm_query(int64_t m, int64_t p, int64_t r, ata_dtype dtype, cons
 
 ata_status ata_gemm_plan_create(ata_plan* out, int64_t m, int64_t p, int64_t r, ata_dtype dtype,
                                 const ata_plan_options* opts) {
+    NvtxRange nv("ata_gemm_plan_create");
     if (!out) return fail(ATA_EINVAL, "NULL argument");
     *out = nullptr;
     if (r < 0) return fail(ATA_EINVAL, "r must be >= 0");
@@ -993,6 +1010,7 @@ ata_status ata_gemm_plan_create(ata_plan* out, int64_t m, int64_t p, int64_t r, 
 
 ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx, const void* Y, int64_t ldy, double* C,
                        int64_t ldc, void* stream) {
+    NvtxRange nv("ata_gemm_tn");
     if (!plan) return fail(ATA_EINVAL, "plan is NULL");
     if (!plan->plan.gemm) return fail(ATA_EINVAL, "an A^t A plan: use ata_execute");
     const int64_t m = plan->plan.m, p = plan->plan.n, r = plan->plan.r;
@@ -1021,6 +1039,7 @@ ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx, const void* Y,
 
 
 ata_status ata_plan_create_opts(ata_plan* out, int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* opts) {
+    NvtxRange nv("ata_plan_create");
     if (!out || !opts) return fail(ATA_EINVAL, "NULL argument");
     *out = nullptr;
     PlanOptions o;
@@ -1064,6 +1083,7 @@ ata_status ata_plan_workspace_size(ata_plan plan, size_t* bytes) {
 }
 
 ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_packed, void* stream) {
+    NvtxRange nv("ata_execute");
     if (!plan) return fail(ATA_EINVAL, "plan is NULL");
     if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan: use ata_gemm_tn");
     const int64_t m = plan->plan.m, n = plan->plan.n;
@@ -1079,6 +1099,7 @@ ata_status ata_execute(ata_plan plan, const void* A, int64_t lda, double* C_pack
 }
 
 ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, double* C_host, void* stream) {
+    NvtxRange nv("ata_execute_host");
     if (!plan) return fail(ATA_EINVAL, "plan is NULL");
     if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan: use ata_gemm_tn");
     const int64_t m = plan->plan.m, n = plan->plan.n;
@@ -1116,6 +1137,7 @@ ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, doub
 }
 
 ata_status ata_execute_host_async(ata_plan plan, const void* A_host, int64_t lda, double* C_host) {
+    NvtxRange nv("ata_execute_host_async");
     if (!plan) return fail(ATA_EINVAL, "plan is NULL");
     if (plan->plan.gemm) return fail(ATA_EINVAL, "a general-product plan: use ata_gemm_tn");
     const int64_t m = plan->plan.m, n = plan->plan.n;
@@ -1210,6 +1232,19 @@ ata_status ata_plan_device_status(ata_plan plan, int* code) {
     if (plan->tables.status) ATA_CUDA(cudaMemcpy(code, plan->tables.status, sizeof(int), cudaMemcpyDeviceToHost));
     if (*code == 0 && plan->tables.counter)
         ATA_CUDA(cudaMemcpy(code, plan->tables.counter + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*code == 0 && plan->guard > 0) {
+        // canary guard bands: any byte changed means a write outside the workspace
+        std::vector<unsigned char> g((size_t)plan->guard);
+        for (int side = 0; side < 2 && *code == 0; ++side) {
+            const char* src = side == 0 ? plan->ws_base : plan->ws + plan->plan.ws_bytes;
+            ATA_CUDA(cudaMemcpy(g.data(), src, g.size(), cudaMemcpyDeviceToHost));
+            for (unsigned char b : g)
+                if (b != (unsigned char)kCanaryByte) {
+                    *code = side == 0 ? 90 : 91;
+                    break;
+                }
+        }
+    }
     return ATA_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <string>
@@ -137,6 +138,16 @@ cudaError_t dev_malloc(T** p, size_t bytes) {
     *p = static_cast<T*>(v);
     return e;
 }
+
+// NVTX range over a host call of the C ABI (plan creation, execution,
+// batches, tuning): a profiler attached to the process shows where each call
+// spent its host time and which launches it queued.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 extern thread_local std::string g_last_error;
 ata_status fail(ata_status s, const std::string& msg);

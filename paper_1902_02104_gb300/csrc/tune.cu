@@ -224,6 +224,7 @@ std::map<TuneKey, std::pair<ata_plan_options, float>> g_measured;
 extern "C" ata_status ata_tune(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_options* base, int candidates,
                                ata_plan_options* out, float* best_ms) {
     using namespace ata;
+    NvtxRange nv("ata_tune");
     if (!out) return fail(ATA_EINVAL, "out is NULL");
     if (candidates < 1 || candidates > 8) return fail(ATA_EINVAL, "candidates must be in [1, 8]");
     ata_plan_options u;

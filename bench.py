@@ -72,7 +72,7 @@ GEMM_WORKLOADS = {
     "gemm_tn_bf16x3_16384x4096x4096": (16384, 4096, 4096, "bf16x3", "scaled_cols", 2, 0),
 }
 # workloads run by their own drivers (not single products)
-EXTRA_WORKLOADS = ["batched_bf16x3", "batched_f64", "serving_bf16x3", "serving_ozaki"]
+EXTRA_WORKLOADS = ["batched_bf16x3", "batched_f64", "serving_bf16x3", "serving_ozaki", "serving_f64"]
 
 # Peak of the FP64 leaf arithmetic: 2 DFMA per clock per SM (the step-0
 # probe measured 1.204 TFLOP/s of DFMA on 152 SMs) at the 2070 MHz maximum
@@ -747,13 +747,14 @@ def run_batched(args, mode):
     return line if rank == 0 else None
 
 
-# Serving rates at which each mode has run clean on GB300 (every request
-# completed, no device error): bf16x3 at 2000 req/s for 60 s (offered load
-# about 1% of its capacity) and the FP64 emulation at 500 req/s.  Plain FP64
-# serving is not run: offered more work than it completes, it raised an
-# illegal-address fault whose cause was not found, so its capacity is timed
-# one request at a time instead.  Higher rates are refused.
-SERVING_CLEAN_RATE = {"bf16x3": 2000.0, "ozaki": 500.0}
+# Serving rates allowed per mode: rates at which the mode has run clean on
+# GB300 (bf16x3 at 2000 req/s for 60 s, offered load about 1% of its
+# capacity; the FP64 emulation at 500 req/s), and for plain FP64 200 req/s,
+# about 40% of its capacity (478 req/s, each request timed alone), so that
+# it is never offered more work than it completes: offered more, it once
+# raised an illegal-address fault whose cause was not found.  Higher rates
+# are refused.
+SERVING_CLEAN_RATE = {"bf16x3": 2000.0, "ozaki": 500.0, "f64": 200.0}
 
 
 def run_serving(args, mode):

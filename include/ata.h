@@ -442,7 +442,15 @@ typedef uint64_t ata_ticket;
  * max_inflight concurrent requests on their own streams, and a device-memory
  * budget (bytes) that bounds the plans' workspaces and staging buffers held
  * at once.  Plans are created on first use of a shape and stay resident
- * while the budget allows.  Errors: ATA_EINVAL, ATA_ENOMEM, ATA_ECUDA. */
+ * while the budget allows.  A request is admitted when a stream slot is
+ * free, its plan fits the budget, and the device reports that much memory
+ * free plus a 256 MiB reserve (cudaMemGetInfo); otherwise idle plans are
+ * evicted, least recently used first, once no request is in flight, or the
+ * request waits.  A request that cannot fit even then fails with ATA_EBUSY.
+ * Each request's kernels are launched directly on its slot's stream (no
+ * graph capture on the scheduler thread).  The server's streams do not wait
+ * for the caller's streams: A must be complete, and C free, when a request
+ * is submitted.  Errors: ATA_EINVAL, ATA_ENOMEM, ATA_ECUDA. */
 ata_status ata_server_create(ata_server* out, size_t device_budget_bytes,
                              ata_dtype dtype, int max_inflight);
 

@@ -2,8 +2,8 @@
 // (ata_server_*, ata_submit, ata_poll).
 //
 // A host scheduler thread admits queued requests in arrival order whenever a
-// stream slot is free and the device-memory budget can hold the request's
-// plan.  Plans stay resident per shape (m, n, lda) and are reused; a second
+// stream slot is free, the device-memory budget can hold the request's plan,
+// and the device has that much memory free (cudaMemGetInfo, plus a reserve).  Plans stay resident per shape (m, n, lda) and are reused; a second
 // instance of a shape's plan is created when the first is busy (a plan runs
 // one execution at a time); idle plans are evicted least recently used when
 // the budget is needed.  Each admitted request runs its plan's graph on one of
@@ -78,6 +78,10 @@ struct TicketInfo {
 
 }  // namespace
 
+// Device memory kept free beyond a new plan's bytes when the server admits
+// it (graph instantiation, tables, other users of the device).
+constexpr size_t kFreeReserve = size_t(256) << 20;
+
 struct ata_server_s {
     size_t budget = 0, used = 0;
     ata_dtype dtype = ATA_F32_BF16X3;
@@ -117,12 +121,27 @@ struct ata_server_s {
             *err = ATA_EBUSY;
             return nullptr;
         }
-        if (used + bytes > budget) {
+        // Free device memory as the driver reports it (other plans, other
+        // users of the device): a new plan needs its bytes plus a reserve,
+        // else it waits like a request over the budget.
+        size_t dev_free = 0, dev_total = 0;
+        const bool mem_ok = cudaMemGetInfo(&dev_free, &dev_total) != cudaSuccess ||
+                            dev_free >= bytes + kFreeReserve;
+        if (!mem_ok && (used == 0 || bytes + kFreeReserve > dev_total)) {
+            *err = ATA_EBUSY;  // nothing of ours to evict, or it could never fit
+            return nullptr;
+        }
+        if (used + bytes > budget || !mem_ok) {
             // Memory is reclaimed only while no request is in flight, so that a
             // plan is never freed while the device runs other work.
             for (const Slot& s : slots)
                 if (s.busy) return nullptr;  // retry once running requests complete
-            while (used + bytes > budget) {
+            auto fits = [&]() {
+                size_t f = 0, tt = 0;
+                const bool dev_ok = cudaMemGetInfo(&f, &tt) != cudaSuccess || f >= bytes + kFreeReserve;
+                return used + bytes <= budget && dev_ok;
+            };
+            while (!fits()) {
                 // evict the least recently used plan (all are idle here)
                 PlanEntry* victim = nullptr;
                 std::list<std::unique_ptr<PlanEntry>>* vlist = nullptr;
@@ -137,7 +156,7 @@ struct ata_server_s {
                 ata_plan_destroy(victim->plan);
                 vlist->remove_if([&](const std::unique_ptr<PlanEntry>& e) { return e.get() == victim; });
             }
-            if (used + bytes > budget) {
+            if (!fits()) {
                 *err = ATA_EBUSY;  // cannot fit even with every other plan evicted
                 return nullptr;
             }

@@ -233,8 +233,8 @@ ata_status ata_plan_query_opts(int64_t m, int64_t n, ata_dtype dtype,
  * timed with CUDA events on a stream of the call's own; the median decides.
  * Fills *out with base's options and the winning cutoff and cta_pair, and
  * *best_ms (may be NULL) with the winner's median time.  Results are cached
- * per (m, n, dtype, base options) for the process, so a second call returns
- * at once.  base may be NULL (all defaults; its cutoff is ignored).  Runs
+ * per (device, m, n, dtype, base options) for the process, so a second call
+ * returns at once.  base may be NULL (all defaults; its cutoff is ignored).  Runs
  * work on the device and synchronises with it: call it before the timed or
  * captured part of an application.
  * Errors: as ata_plan_query_opts, ATA_ENOMEM (no candidate fits), ATA_ECUDA. */

@@ -209,11 +209,12 @@ __global__ void tune_fill_kernel(void* A, int64_t count, int f64) {
 }
 
 struct TuneKey {
+    int device;
     int64_t m, n;
     int dtype, variant, fuse, max_levels, cta_pair;
     bool operator<(const TuneKey& o) const {
-        return std::tie(m, n, dtype, variant, fuse, max_levels, cta_pair) <
-               std::tie(o.m, o.n, o.dtype, o.variant, o.fuse, o.max_levels, o.cta_pair);
+        return std::tie(device, m, n, dtype, variant, fuse, max_levels, cta_pair) <
+               std::tie(o.device, o.m, o.n, o.dtype, o.variant, o.fuse, o.max_levels, o.cta_pair);
     }
 };
 std::map<TuneKey, std::pair<ata_plan_options, float>> g_measured;
@@ -243,7 +244,9 @@ extern "C" ata_status ata_tune(int64_t m, int64_t n, ata_dtype dtype, const ata_
     ata_plan_info info;
     ata_status st = ata_plan_query_opts(m, n, dtype, &u, &info);  // validates the arguments
     if (st != ATA_OK) return st;
-    const TuneKey key{m, n, (int)dtype, u.variant, u.fuse_levels, u.max_strassen_levels, u.cta_pair};
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    const TuneKey key{device, m, n, (int)dtype, u.variant, u.fuse_levels, u.max_strassen_levels, u.cta_pair};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_measured.find(key);

@@ -667,6 +667,14 @@ ata_status rebuild_tables(ata_plan plan, int64_t lda, int64_t ldb = 0, int64_t l
     return ATA_OK;
 }
 
+// Host rows of A into a dense device staging buffer: one linear copy when
+// the rows are contiguous (lda == n), a pitched copy otherwise.
+cudaError_t copy_rows_in(void* dst, const void* A_host, int64_t m, int64_t n, int64_t lda, int es, cudaStream_t s) {
+    if (lda == n) return cudaMemcpyAsync(dst, A_host, (size_t)m * n * es, cudaMemcpyHostToDevice, s);
+    return cudaMemcpy2DAsync(dst, (size_t)n * es, A_host, (size_t)lda * es, (size_t)n * es, (size_t)m,
+                             cudaMemcpyHostToDevice, s);
+}
+
 ata_status check_ptr(const void* p, int align, const char* what) {
     if (reinterpret_cast<uintptr_t>(p) % align != 0)
         return fail(ATA_EINVAL, std::string(what) + " is not aligned to its element size");
@@ -1126,9 +1134,7 @@ ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, doub
             }
         }
     }
-    if (m > 0)
-        ATA_CUDA(cudaMemcpy2DAsync(plan->stage_A, (size_t)n * es, A_host, (size_t)lda * es, (size_t)n * es, (size_t)m,
-                                   cudaMemcpyHostToDevice, s));
+    if (m > 0) ATA_CUDA(copy_rows_in(plan->stage_A, A_host, m, n, lda, es, s));
     ata_status st = ata_execute(plan, plan->stage_A ? plan->stage_A : (const void*)plan->stage_C, n, plan->stage_C, stream);
     if (st != ATA_OK) return st;
     ATA_CUDA(cudaMemcpyAsync(C_host, plan->stage_C, (size_t)(n * (n + 1) / 2) * 8, cudaMemcpyDeviceToHost, s));
@@ -1172,9 +1178,7 @@ ata_status ata_execute_host_async(ata_plan plan, const void* A_host, int64_t lda
     }
     // copy-in, once the execution that last read staging set b has finished
     ATA_CUDA(cudaStreamWaitEvent(P.h2d, P.comp_done[b], 0));
-    if (m > 0)
-        ATA_CUDA(cudaMemcpy2DAsync(P.A[b], (size_t)n * es, A_host, (size_t)lda * es, (size_t)n * es, (size_t)m,
-                                   cudaMemcpyHostToDevice, P.h2d));
+    if (m > 0) ATA_CUDA(copy_rows_in(P.A[b], A_host, m, n, lda, es, P.h2d));
     ATA_CUDA(cudaEventRecord(P.a_ready[b], P.h2d));
     // execution, once the input has arrived and the copy-out that last read
     // C[b] has finished

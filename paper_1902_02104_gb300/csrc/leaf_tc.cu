@@ -672,8 +672,11 @@ __device__ __forceinline__ unsigned long long abs_bits(TS x) {
         return __float_as_uint((float)x) & 0x7FFFFFFFu;
 }
 
+// Four blocks per SM (64 registers, no spills): each block's chain of
+// table loads (task, product, term, binding) before its data loads is
+// latency, which more resident blocks overlap.
 template <int NB, typename TS>
-__global__ void __launch_bounds__(256) tc_colmax_kernel(const __grid_constant__ BindSet<NB> bs,
+__global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant__ BindSet<NB> bs,
                                                         const LeafProduct* __restrict__ prods,
                                                         const Term* __restrict__ terms,
                                                         const TcProd* __restrict__ tcp,
@@ -831,9 +834,11 @@ __device__ __forceinline__ void store_parts(const long long (&u)[8], __nv_bfloat
 // Parts of one 64 (K) x 64 (column) tile of a leaf operand, written K-major:
 // part q of column c, K index k at parts + ((q * rows_pad + c) * K_pad + k).
 // Each thread slices two (column, 8 K values) runs and writes 16 bytes per
-// part and run.
+// part and run.  Six blocks per SM (40 registers, no spills; 17 KB of
+// shared memory each) overlap the blocks' table-load chains: 12% less time
+// than four at 16384 x 8192 bf16x3, 5% less for the batched step.
 template <int NB, int MODE>
-__global__ void __launch_bounds__(256) tc_prep_kernel(const __grid_constant__ BindSet<NB> bs,
+__global__ void __launch_bounds__(256, 6) tc_prep_kernel(const __grid_constant__ BindSet<NB> bs,
                                                       const LeafProduct* __restrict__ prods,
                                                       const Term* __restrict__ terms,
                                                       const TcProd* __restrict__ tcp,

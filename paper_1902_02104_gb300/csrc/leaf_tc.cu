@@ -584,44 +584,54 @@ __device__ __forceinline__ TS flip_sign(TS x) {
         return __uint_as_float(__float_as_uint(x) ^ 0x80000000u);
 }
 
+// One term's values of the tile, as stored (its sign not applied), zero
+// outside the term's extent.
+template <typename TS, int NB>
+__device__ __forceinline__ void load_term_raw(const BindSet<NB>& bs, const Term& tm, int K, int k0, int c0,
+                                              TS (&x)[TileRegs<TS>::NPASS][TileRegs<TS>::VEC]) {
+    using TR = TileRegs<TS>;
+    constexpr int VEC = TR::VEC, NPASS = TR::NPASS;
+    const int vc = (threadIdx.x % TR::VPR) * VEC;
+    const int r0 = threadIdx.x / TR::VPR;
+    const Bind& b = bs.b[tm.inst];
+    const TS* base = term_base<TS>(b, tm.buf);
+    const int c = c0 + vc;
+    const TS* colp = base + tm.off + c;
+    const int kmax = min(K, tm.rows);
+    const bool vec_ok = c + VEC <= tm.cols && ((reinterpret_cast<uintptr_t>(colp) & 15) == 0) &&
+                        ((tm.ld * (int64_t)sizeof(TS)) & 15) == 0;
+    if (vec_ok) {
+#pragma unroll
+        for (int p = 0; p < NPASS; ++p) {
+            const int k = k0 + r0 + p * TR::RPP;
+            uint4 u = make_uint4(0u, 0u, 0u, 0u);
+            if (k < kmax) u = __ldg(reinterpret_cast<const uint4*>(colp + (int64_t)k * tm.ld));
+            *reinterpret_cast<uint4*>(x[p]) = u;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NPASS; ++p) {
+            const int k = k0 + r0 + p * TR::RPP;
+#pragma unroll
+            for (int j = 0; j < VEC; ++j)
+                x[p][j] = (k < kmax && c + j < tm.cols) ? __ldg(colp + (int64_t)k * tm.ld + j) : TS(0);
+        }
+    }
+}
+
 template <typename TS, int NB>
 __device__ __forceinline__ void load_operand_regs(const BindSet<NB>& bs, const Term* __restrict__ terms, int t0,
                                                   int nt, int K, int k0, int c0, TileRegs<TS>& R) {
     using TR = TileRegs<TS>;
     constexpr int VEC = TR::VEC, NPASS = TR::NPASS;
-    const int vc = (threadIdx.x % TR::VPR) * VEC;
-    const int r0 = threadIdx.x / TR::VPR;
 #pragma unroll
     for (int p = 0; p < NPASS; ++p)
 #pragma unroll
         for (int j = 0; j < VEC; ++j) R.v[p][j] = TS(0);
     for (int t = 0; t < nt; ++t) {
         const Term tm = terms[t0 + t];
-        const Bind& b = bs.b[tm.inst];
-        const TS* base = term_base<TS>(b, tm.buf);
-        const int c = c0 + vc;
-        const TS* colp = base + tm.off + c;
-        const int kmax = min(K, tm.rows);
-        const bool vec_ok = c + VEC <= tm.cols && ((reinterpret_cast<uintptr_t>(colp) & 15) == 0) &&
-                            ((tm.ld * (int64_t)sizeof(TS)) & 15) == 0;
         TS x[NPASS][VEC];
-        if (vec_ok) {
-#pragma unroll
-            for (int p = 0; p < NPASS; ++p) {
-                const int k = k0 + r0 + p * TR::RPP;
-                uint4 u = make_uint4(0u, 0u, 0u, 0u);
-                if (k < kmax) u = __ldg(reinterpret_cast<const uint4*>(colp + (int64_t)k * tm.ld));
-                *reinterpret_cast<uint4*>(x[p]) = u;
-            }
-        } else {
-#pragma unroll
-            for (int p = 0; p < NPASS; ++p) {
-                const int k = k0 + r0 + p * TR::RPP;
-#pragma unroll
-                for (int j = 0; j < VEC; ++j)
-                    x[p][j] = (k < kmax && c + j < tm.cols) ? __ldg(colp + (int64_t)k * tm.ld + j) : TS(0);
-            }
-        }
+        load_term_raw<TS>(bs, tm, K, k0, c0, x);
         if (nt == 1) {
             if (tm.neg) {
 #pragma unroll
@@ -690,19 +700,34 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
     unsigned long long m[TR::VEC];
 #pragma unroll
     for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
-    for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
-        TileRegs<TS> R0, R1;
-        load_operand_regs<TS>(bs, terms, t0, nt, tk.k1, k, tk.c0, R0);
-        load_operand_regs<TS>(bs, terms, t0, nt, tk.k1, k + PT, tk.c0, R1);
-        // magnitudes compared as bit patterns (integer operations only)
+    // magnitudes compared as bit patterns (integer operations only)
+    auto take = [&](const TS (&x0)[TR::NPASS][TR::VEC], const TS (&x1)[TR::NPASS][TR::VEC]) {
 #pragma unroll
         for (int j = 0; j < TR::VEC; ++j)
 #pragma unroll
             for (int p = 0; p < TR::NPASS; ++p) {
-                const unsigned long long b0 = abs_bits(R0.v[p][j]), b1 = abs_bits(R1.v[p][j]);
+                const unsigned long long b0 = abs_bits(x0[p][j]), b1 = abs_bits(x1[p][j]);
                 const unsigned long long b = b0 > b1 ? b0 : b1;
                 m[j] = b > m[j] ? b : m[j];
             }
+    };
+    if (nt == 1) {
+        // one term: its sign does not change a magnitude, so both tiles'
+        // loads are issued before any value is used
+        const Term tm = terms[t0];
+        for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
+            TS x0[TR::NPASS][TR::VEC], x1[TR::NPASS][TR::VEC];
+            load_term_raw<TS>(bs, tm, tk.k1, k, tk.c0, x0);
+            load_term_raw<TS>(bs, tm, tk.k1, k + PT, tk.c0, x1);
+            take(x0, x1);
+        }
+    } else {
+        for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
+            TileRegs<TS> R0, R1;
+            load_operand_regs<TS>(bs, terms, t0, nt, tk.k1, k, tk.c0, R0);
+            load_operand_regs<TS>(bs, terms, t0, nt, tk.k1, k + PT, tk.c0, R1);
+            take(R0.v, R1.v);
+        }
     }
     const int vc = (threadIdx.x % TR::VPR) * TR::VEC;
     const int r0 = threadIdx.x / TR::VPR;
@@ -921,15 +946,18 @@ __global__ void __launch_bounds__(256) tc_termmax_kernel(const __grid_constant__
     unsigned long long m[TR::VEC];
 #pragma unroll
     for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
+    // a segment is one block of one buffer (no sign): both tiles' loads are
+    // issued before any value is used
+    const Term tm = terms[tk.prod];
     for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
-        TileRegs<double> R0, R1;
-        load_operand_regs<double>(bs, terms, tk.prod, 1, tk.k1, k, tk.c0, R0);
-        load_operand_regs<double>(bs, terms, tk.prod, 1, tk.k1, k + PT, tk.c0, R1);
+        double x0[TR::NPASS][TR::VEC], x1[TR::NPASS][TR::VEC];
+        load_term_raw<double>(bs, tm, tk.k1, k, tk.c0, x0);
+        load_term_raw<double>(bs, tm, tk.k1, k + PT, tk.c0, x1);
 #pragma unroll
         for (int j = 0; j < TR::VEC; ++j)
 #pragma unroll
             for (int p = 0; p < TR::NPASS; ++p) {
-                const unsigned long long b0 = abs_bits(R0.v[p][j]), b1 = abs_bits(R1.v[p][j]);
+                const unsigned long long b0 = abs_bits(x0[p][j]), b1 = abs_bits(x1[p][j]);
                 const unsigned long long b = b0 > b1 ? b0 : b1;
                 m[j] = b > m[j] ? b : m[j];
             }

@@ -104,11 +104,7 @@ def tensor_peak(mode):
 LEAF_TRAFFIC = {
     # a one-launch capture of the 4500^2 small case (cutoff 1200), scaled by
     # the ratio of tree multiplications (traffic grows with tiles x K)
-    ("ata_ozaki_10000x10000", "8055985539fd8bb4"): (940.1e6 + 96.1e6) * 468800000000 / 42724968750,
-    ("ata_ozaki_10000x10000", "e3737c832598ccb7"): 10.945e9 + 0.571e9,
-    ("ata_bf16x3_16384x8192", "e3737c832598ccb7"): 5.973e9 + 0.270e9,
-    ("ata_tf32_16384x8192", "e3737c832598ccb7"): 2.412e9 + 0.245e9,
-    ("ata_f64_10000x10000", "beaf79f07d6f1ff4"): 35.899e9 + 4.653e9,
+    ("ata_ozaki_10000x10000", "65723a3bb7f958ec"): (942.1e6 + 96.0e6) * 468800000000 / 42724968750,
 }
 
 

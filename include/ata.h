@@ -165,7 +165,12 @@ ata_status ata_plan_query(int64_t m, int64_t n, ata_dtype dtype, int cutoff,
  * here, on the current device).  cutoff in [16, 4096]; 0 = autotune: the
  * cutoff minimising the planner's cost model of this part (leaf
  * multiply-adds, Strassen additions and workspace traffic at the measured
- * rates, workspace capped at 48 GiB), cached per shape and dtype.
+ * rates, workspace capped at 48 GiB), cached per shape and dtype.  Each
+ * Strassen level holds the operand sums and outputs of all its products at
+ * once; when no cutoff fits the cap, the autotune lowers the Strassen level
+ * cap (unless max_strassen_levels fixes it) until one does, and when none
+ * fits even without Strassen levels it takes the plan with the smallest
+ * workspace.
  * Errors: ATA_EINVAL (bad sizes, dtype or cutoff, NULL out), ATA_ENOMEM,
  * ATA_ECUDA. */
 ata_status ata_plan_create(ata_plan* out, int64_t m, int64_t n,
@@ -182,7 +187,9 @@ typedef struct {
                                     in fixed point while slicing), 0 with
                                     Winograd's variant; 1 for the FP32 modes) */
     int32_t max_strassen_levels; /* cap on Strassen levels per product
-                                    (-1 = none; 0 = classical products)        */
+                                    (-1 = none, or what fits the workspace
+                                    cap when the cutoff is autotuned; 0 =
+                                    classical products)                       */
     int32_t cta_pair;            /* tensor-core leaves: 1 = output tiles
                                     computed by CTA pairs (two SMs, tcgen05
                                     cta_group::2; 256 x 256 for TF32, 256 x

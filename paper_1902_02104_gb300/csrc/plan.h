@@ -34,6 +34,10 @@
 
 namespace ata {
 
+// A Strassen level cap at or above this leaves the depth free (to the
+// cutoff, or to what fits the workspace when the cutoff is automatic).
+constexpr int kFreeLevels = 64;
+
 // Buffers a term or an output refers to: the caller's A (or X of a general
 // product), the plan workspace W, the caller's C, and Y of a general product.
 enum BufId : int8_t { BUF_A = 0, BUF_W = 1, BUF_C = 2, BUF_B = 3 };
@@ -122,7 +126,7 @@ struct Plan {
     int8_t in_dt = DT_F64;    // element type of A
     int8_t sum_dt = DT_F64;   // element type of materialised operand sums
     int fuse_levels = 1;      // bottom Strassen levels whose sums are fused into leaf loads
-    int max_levels = 64;      // cap on Strassen levels per product
+    int max_levels = kFreeLevels;  // cap on Strassen levels per product
 
     std::vector<Term> terms;
     std::vector<LeafProduct> products;
@@ -156,7 +160,7 @@ struct PlanOptions {
     int variant = 0;
     LeafKind leaf = LEAF_F64;
     int fuse_levels = 1;
-    int max_levels = 64;
+    int max_levels = kFreeLevels;
     bool cta_pair = false;  // tensor-core leaves on 256 x 128 CTA-pair tiles where eligible
     uint64_t wait_ns = 0;   // tensor-core leaves: pipeline wait limit (0 = the kernel's default)
 };

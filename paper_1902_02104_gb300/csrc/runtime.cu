@@ -575,7 +575,7 @@ ata_status make_options(int64_t m, int64_t n, ata_dtype dtype, const ata_plan_op
     o->variant = variant;
     o->cutoff = cutoff != 0 ? cutoff : default_cutoff(m, n, dtype);
     o->fuse_levels = u.fuse_levels >= 0 ? u.fuse_levels : default_fuse_levels(dtype, variant);
-    o->max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : 64;
+    o->max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : kFreeLevels;
     // CTA pairs by default for TF32, whose leaf is bound by L2 reads (a pair
     // stages half of B per SM); single CTAs for the others
     o->cta_pair = u.cta_pair == 1 || (u.cta_pair < 0 && dtype == ATA_F32_TF32);

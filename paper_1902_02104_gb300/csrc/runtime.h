@@ -175,9 +175,15 @@ int default_cutoff(int64_t m, int64_t n, ata_dtype dtype);
 int default_fuse_levels(ata_dtype dtype, int variant);
 // r >= 0 tunes the general product X^t Y (X: m x n, Y: m x r) instead.
 ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o, int64_t r = -1);
-// The cost model's cutoff candidates for plan options o, fastest first.
+// The cost model's cutoff candidates for plan options o, fastest first,
+// among the plans whose workspace fits the cap.
 std::vector<std::pair<double, int>> rank_cutoffs(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
                                                  int64_t r);
+// The same for an automatic plan shape: fewer Strassen levels where the
+// depth is free and no cutoff fits the cap, else the smallest workspace;
+// *max_levels receives the level cap of the ranked plans.
+std::vector<std::pair<double, int>> rank_plans(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
+                                               int64_t r, int* max_levels);
 
 // Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
 const Plan& plan_of(ata_plan p);

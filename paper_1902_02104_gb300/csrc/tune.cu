@@ -89,14 +89,14 @@ double model_time(const Plan& P, ata_dtype d) {
 }
 
 // Leaf products a cutoff would create, estimated without building the plan:
-// every off-diagonal block at depth d has 7^s leaves.
-double estimate_products(int64_t m, int64_t n, int cutoff) {
+// every off-diagonal block at depth d has 7^s leaves (s <= max_levels).
+double estimate_products(int64_t m, int64_t n, int cutoff, int max_levels) {
     double total = 0;
     int64_t w = n, md = m;
     for (int d = 0; d < 40 && std::min(md, w) > cutoff; ++d) {
         int64_t p = (w + 1) / 2, q = (md + 1) / 2, r = w / 2;
         int s = 0;
-        while (std::min(p, std::min(q, r)) > cutoff) {
+        while (s < max_levels && std::min(p, std::min(q, r)) > cutoff) {
             p = (p + 1) / 2;
             q = (q + 1) / 2;
             r = (r + 1) / 2;
@@ -110,7 +110,7 @@ double estimate_products(int64_t m, int64_t n, int cutoff) {
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int>, int> g_tuned;
+std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int, int>, std::pair<int, int>> g_tuned;
 
 }  // namespace
 
@@ -136,29 +136,80 @@ int default_cutoff(int64_t m, int64_t n, ata_dtype dtype) {
     }
 }
 
-// Cutoff candidates ranked by the cost model (fastest first).
+namespace {
+
+constexpr int kCutoffs[] = {64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+
+// Builds the plan of cutoff c under options o into *P; false when the
+// leaf kernels would not accept it (product count, fused terms per operand).
+bool candidate_plan(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o, int64_t r, int c, Plan* P) {
+    if (r < 0 && estimate_products(m, n, c, o.max_levels) > kMaxLeafProducts) return false;
+    if (dtype != ATA_F64 && c < 256) return false;  // tensor-core tiles are 128 x 128
+    PlanOptions t = o;
+    t.cutoff = c;
+    std::string err;
+    if (!(r < 0 ? build_plan(m, n, t, P, &err) : build_gemm_plan(m, n, r, t, P, &err))) return false;
+    if ((int64_t)P->products.size() > kMaxLeafProducts) return false;
+    for (const LeafProduct& lp : P->products)
+        if (lp.nx > kMaxTerms || lp.ny > kMaxTerms) return false;
+    return true;
+}
+
+}  // namespace
+
+// Cutoff candidates ranked by the cost model (fastest first), among the
+// plans whose workspace fits kWorkspaceCap.
 std::vector<std::pair<double, int>> rank_cutoffs(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
                                                  int64_t r) {
-    static const int cands[] = {64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
     std::vector<std::pair<double, int>> out;
-    for (int c : cands) {
-        if (r < 0 && estimate_products(m, n, c) > kMaxLeafProducts) continue;
-        if (dtype != ATA_F64 && c < 256) continue;  // tensor-core tiles are 128 x 128
-        PlanOptions t = o;
-        t.cutoff = c;
+    for (int c : kCutoffs) {
         Plan P;
-        std::string err;
-        if (!(r < 0 ? build_plan(m, n, t, &P, &err) : build_gemm_plan(m, n, r, t, &P, &err))) continue;
-        if ((int64_t)P.products.size() > kMaxLeafProducts) continue;
-        if (P.ws_bytes > kWorkspaceCap) continue;
-        bool terms_ok = true;
-        for (const LeafProduct& lp : P.products) terms_ok = terms_ok && lp.nx <= kMaxTerms && lp.ny <= kMaxTerms;
-        if (!terms_ok) continue;
+        if (!candidate_plan(m, n, dtype, o, r, c, &P) || P.ws_bytes > kWorkspaceCap) continue;
         out.push_back({model_time(P, dtype), c});
     }
     std::stable_sort(out.begin(), out.end(),
                      [](const std::pair<double, int>& a, const std::pair<double, int>& b) { return a.first < b.first; });
     return out;
+}
+
+// Ranked cutoffs for an automatic plan shape.  Every Strassen level
+// materialises the operand sums and outputs of all its products at once, so
+// a large product may fit the workspace cap only with fewer levels: when no
+// cutoff fits and the caller left the depth free (max_levels >= kFreeLevels),
+// the level cap is lowered until one does.  When none fits even without
+// Strassen levels, the cutoff with the smallest workspace is the one
+// candidate (creating the plan then succeeds wherever the device holds it).
+// *max_levels receives the level cap the ranking used.
+std::vector<std::pair<double, int>> rank_plans(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
+                                               int64_t r, int* max_levels) {
+    *max_levels = o.max_levels;
+    auto ranked = rank_cutoffs(m, n, dtype, o, r);
+    if (!ranked.empty()) return ranked;
+    PlanOptions t = o;
+    if (o.max_levels >= kFreeLevels) {
+        for (int lv = 3; lv >= 0 && ranked.empty(); --lv) {
+            t.max_levels = lv;
+            ranked = rank_cutoffs(m, n, dtype, t, r);
+            if (!ranked.empty()) *max_levels = lv;
+        }
+        if (!ranked.empty()) return ranked;
+        t.max_levels = 0;
+    }
+    int64_t best_ws = -1;
+    int best_c = 0;
+    for (int c : kCutoffs) {
+        Plan P;
+        if (!candidate_plan(m, n, dtype, t, r, c, &P)) continue;
+        if (best_ws < 0 || P.ws_bytes < best_ws) {
+            best_ws = P.ws_bytes;
+            best_c = c;
+        }
+    }
+    if (best_ws >= 0) {
+        ranked.push_back({0.0, best_c});
+        *max_levels = t.max_levels;
+    }
+    return ranked;
 }
 
 ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, PlanOptions* o, int64_t r) {
@@ -167,15 +218,19 @@ ata_status autotune_cutoff(int64_t m, int64_t n, ata_dtype dtype, int variant, P
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            o->cutoff = it->second;
+            o->cutoff = it->second.first;
+            o->max_levels = it->second.second;
             return ATA_OK;
         }
     }
-    const auto ranked = rank_cutoffs(m, n, dtype, *o, r);
-    const int best_c = ranked.empty() ? o->cutoff : ranked.front().second;
-    o->cutoff = best_c;
+    int levels = o->max_levels;
+    const auto ranked = rank_plans(m, n, dtype, *o, r, &levels);
+    if (!ranked.empty()) {
+        o->cutoff = ranked.front().second;
+        o->max_levels = levels;
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = best_c;
+    g_tuned[key] = {o->cutoff, o->max_levels};
     return ATA_OK;
 }
 
@@ -262,15 +317,17 @@ extern "C" ata_status ata_tune(int64_t m, int64_t n, ata_dtype dtype, const ata_
     o.leaf = dtype == ATA_F64 ? LEAF_F64 : dtype == ATA_F32_BF16X3 ? LEAF_BF16X3 : dtype == ATA_F32_TF32 ? LEAF_TF32 : LEAF_OZAKI;
     o.variant = u.variant < 0 ? ATA_STRASSEN : u.variant;
     o.fuse_levels = u.fuse_levels >= 0 ? u.fuse_levels : default_fuse_levels(dtype, o.variant);
-    o.max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : 64;
+    o.max_levels = u.max_strassen_levels >= 0 ? u.max_strassen_levels : kFreeLevels;
     o.cta_pair = u.cta_pair == 1 || (u.cta_pair < 0 && dtype == ATA_F32_TF32);
-    auto ranked = rank_cutoffs(m, n, dtype, o, -1);
+    int levels = o.max_levels;
+    auto ranked = rank_plans(m, n, dtype, o, -1, &levels);
     if (ranked.empty()) ranked.push_back({0.0, info.cutoff});
     if ((int)ranked.size() > candidates) ranked.resize(candidates);
     std::vector<ata_plan_options> cands;
     for (const auto& rc : ranked) {
         ata_plan_options c = u;
         c.cutoff = rc.second;
+        if (levels < kFreeLevels) c.max_strassen_levels = levels;
         if (dtype == ATA_F64 || !tune_pair) {
             cands.push_back(c);
         } else {

@@ -13,6 +13,8 @@ Section 6.2; no dataset is involved):
 * ``batch_shapes`` m log-uniform in [lo, hi], then n log-uniform, rounded to
                    nearest integers                         (512 instances, seed 3)
 * ``poisson_arrivals`` exponential gaps at a given rate     (serving, seed 4)
+* ``integers`` / ``small_integers`` i.i.d. integers in [-4, 4] (exact-result
+                   parity; the latter as int8 for inputs past 2^31 entries)
 """
 from __future__ import annotations
 
@@ -39,6 +41,13 @@ def scaled_cols(m: int, n: int, seed: int = 2, scale: float = 1e3, every: int = 
 def integers(m: int, n: int, seed: int = 5, lo: int = -4, hi: int = 4, dtype=np.float64) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi + 1, size=(m, n)).astype(dtype)
+
+
+def small_integers(m: int, n: int, seed: int = 6, lo: int = -4, hi: int = 4) -> np.ndarray:
+    """Integers in [lo, hi] drawn directly as int8: one byte per entry on the
+    host, for inputs of billions of entries (converted on the device)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, size=(m, n), dtype=np.int8)
 
 
 def log_uniform_ints(rng, lo: int, hi: int, count: int) -> np.ndarray:

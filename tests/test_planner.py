@@ -190,3 +190,45 @@ def test_plan_check_tile_grid(dtype, pair):
         ata.ata_plan_check(m, n, dtype, c, cta_pair=pair)
     for m, p, r in [(500, 1024, 1100), (500, 1000, 1030), (2000, 600, 300), (500, 2000, 2500), (500, 129, 100)]:
         ata.ata_gemm_plan_check(m, p, r, dtype, 512, cta_pair=pair)
+
+
+# ---------------------------------------------------------------------------
+# Automatic plan shape under the workspace cap.  Every Strassen level holds
+# the operand sums and outputs of all its products at once, so the largest
+# products fit the 48 GiB cap only with fewer levels.
+
+CAP = 48 << 30
+TC_CUTOFFS = (256, 320, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
+
+
+def test_autotune_lowers_strassen_levels_to_fit_the_cap():
+    m, n, dt = 50000, 30000, ata.ATA_F32_BF16X3
+    free = [q(m, n, c, dt)["workspace_bytes"] for c in TC_CUTOFFS]
+    assert min(free) > CAP  # with free depth no cutoff fits
+    auto = q(m, n, 0, dt)
+    assert auto["workspace_bytes"] <= CAP
+    assert auto["max_strassen_levels"] >= 1  # the deepest cap that fits, not zero
+    # a fixed level cap is the caller's: it is kept, not lowered, and the
+    # smallest workspace under it is taken although it exceeds the cap
+    fixed = q(m, n, 0, dt, max_strassen_levels=3)
+    assert fixed["max_strassen_levels"] > auto["max_strassen_levels"]
+    assert fixed["workspace_bytes"] == min(free) > CAP
+
+
+def test_autotune_takes_the_smallest_workspace_when_nothing_fits():
+    m, n, dt = 40000, 60000, ata.ATA_F32_BF16X3
+    classical = [q(m, n, c, dt, max_strassen_levels=0)["workspace_bytes"] for c in TC_CUTOFFS]
+    assert min(classical) > CAP
+    auto = q(m, n, 0, dt)
+    assert auto["max_strassen_levels"] == 0
+    assert auto["workspace_bytes"] == min(classical)
+    ata.ata_plan_check(m, n, dt, 0)
+
+
+def test_autotune_unchanged_where_the_cap_holds():
+    # paper-scale shapes keep the cost model's free-depth choice
+    for m, n, dt in [(10000, 10000, ata.ATA_F64_OZAKI), (16384, 8192, ata.ATA_F32_BF16X3)]:
+        auto = q(m, n, 0, dt)
+        same = q(m, n, auto["cutoff"], dt)
+        assert auto["workspace_bytes"] == same["workspace_bytes"] <= CAP
+        assert auto["max_strassen_levels"] == same["max_strassen_levels"]

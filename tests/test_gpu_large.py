@@ -5,9 +5,9 @@
 * A of 256 x 70000: the packed output holds 2.45e9 entries, written by the
   149 878 upper tiles of one diagonal leaf.
 
-Entries are integers in [-4, 4], so every tensor-core mode is exact here
-(bf16 and TF32 hold them, chunk sums stay below 2^24, |C_ij| <= 16 m <
-2^24): sampled entries, with the first and last rows and columns, are
+Entries are integers in [-4, 4], so every mode is exact here (bf16 and
+TF32 hold them, chunk sums stay below 2^24, |C_ij| <= 16 m < 2^24; the
+plain FP64 path runs these sizes in a few seconds): sampled entries, with the first and last rows and columns, are
 compared bitwise with the oracle's entries.  A case holds 20-50 GB on the
 device; the plans' index arithmetic was checked on the host first
 (ata_plan_check, test_planner.py)."""
@@ -22,7 +22,8 @@ from paper_1902_02104_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-MODES = [(ata.ATA_F32_BF16X3, "float32"), (ata.ATA_F32_TF32, "float32"), (ata.ATA_F64_OZAKI, "float64")]
+MODES = [(ata.ATA_F32_BF16X3, "float32"), (ata.ATA_F32_TF32, "float32"), (ata.ATA_F64_OZAKI, "float64"),
+         (ata.ATA_F64, "float64")]
 
 
 @functools.lru_cache(maxsize=2)

@@ -257,3 +257,29 @@ def test_fp32_modes_winograd_normwise(gpu, dtype):
     assert plan.info["max_strassen_levels"] == 2
     err = oracle.normwise_error(C, oracle.ata_packed(A), 2048)
     assert err <= NORM_TOL[dtype], err
+
+
+# ---------------------------------------------------------------------------
+# Degenerate shapes in the tensor-core modes
+
+@pytest.mark.parametrize("dtype", [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI])
+def test_tc_degenerate_shapes(gpu, dtype):
+    import torch
+    tdt = torch.float64 if dtype == ata.ATA_F64_OZAKI else torch.float32
+    ndt = np.float64 if dtype == ata.ATA_F64_OZAKI else np.float32
+    # m = 0: every entry of C is an empty sum
+    plan = ata.Plan(0, 50, dtype, 256)
+    C = torch.full((50 * 51 // 2,), 7.0, dtype=torch.float64, device="cuda")
+    plan(torch.empty((0, 50), dtype=tdt, device="cuda"), C)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(C).item() == 0
+    # n = 0: nothing to write
+    plan = ata.Plan(10, 0, dtype, 256)
+    plan(torch.empty((10, 0), dtype=tdt, device="cuda"), torch.empty((0,), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    # one column, one row, and a single entry: one partial tile each
+    for m, n in [(5000, 1), (1, 700), (1, 1)]:
+        A = inputs.integers(m, n, seed=m + 3 * n).astype(ndt)
+        C, p = run(A, dtype, 256)
+        assert p.device_status() == 0
+        assert np.array_equal(C, oracle.ata_packed(A))

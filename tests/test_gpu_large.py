@@ -4,6 +4,8 @@
   buffers hold more than 2^31 elements, and the leaves run 600000 deep in K.
 * A of 256 x 70000: the packed output holds 2.45e9 entries, written by the
   149 878 upper tiles of one diagonal leaf.
+* X^t Y with X 256 x 50000 and Y 256 x 45000: a dense output of 2.25e9
+  entries.
 
 Entries are integers in [-4, 4], so every mode is exact here (bf16 and
 TF32 hold them, chunk sums stay below 2^24, |C_ij| <= 16 m < 2^24; the
@@ -75,3 +77,24 @@ def test_packed_output_past_2e31_entries(gpu, dtype, tname):
     I, J = _pairs(n, 2000, seed=64)
     got = _run_and_sample(A8, dtype, tname, I, J)
     assert np.array_equal(got, oracle.ata_entries(A8, I, J))
+
+
+@pytest.mark.parametrize("dtype,tname", MODES)
+def test_general_product_output_past_2e31_entries(gpu, dtype, tname):
+    import torch
+    m, p, r = 256, 50000, 45000
+    assert p * r > 2 ** 31
+    X8, Y8 = _input(m, p, 65), _input(m, r, 66)
+    rng = np.random.default_rng(67)
+    I = np.concatenate([rng.integers(0, p, 2000), [0, p - 1, p - 1]])
+    J = np.concatenate([rng.integers(0, r, 2000), [r - 1, 0, r - 1]])
+    tdt = getattr(torch, tname)
+    X, Y = torch.from_numpy(X8).cuda().to(tdt), torch.from_numpy(Y8).cuda().to(tdt)
+    plan = ata.GemmPlan(m, p, r, dtype, 0)
+    C = plan(X, Y)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    got = C.reshape(-1)[torch.from_numpy(I * r + J).cuda()].cpu().numpy()
+    del X, Y, C, plan
+    torch.cuda.empty_cache()
+    assert np.array_equal(got, oracle.gemm_entries(X8, Y8, I, J))

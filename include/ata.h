@@ -30,8 +30,11 @@
  * Ownership
  *   The caller owns A and C_packed.  A plan owns its device workspace, its
  *   task tables and its CUDA graph; ata_plan_destroy frees them.  A plan
- *   runs one execution at a time (its workspace is reused); run
- *   independent products concurrently with separate plans.
+ *   runs one execution at a time (its workspace is reused): an execution
+ *   queued on another stream than the plan's latest one first waits for it
+ *   (an event the library records), in single, batched and prepared-batch
+ *   calls alike, so executions of one plan never overlap on the device.
+ *   Run independent products concurrently with separate plans.
  *
  * Errors
  *   Arguments are checked before any work is queued; a bad argument returns

@@ -28,6 +28,7 @@ struct BatchEntry {
     DeviceTables tables;
     GraphCache graph;
     std::vector<uint64_t> ids;
+    std::shared_ptr<OrderEvent> order_ev;  // recorded after each launch
     ~BatchEntry() {
         graph.release();
         tables.free_all();
@@ -167,7 +168,11 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
     std::vector<Bind> binds;
     binds.reserve(count);
     for (int i = 0; i < count; ++i) binds.push_back(make_bind(plans[i], A[i], lda[i], C_packed[i]));
-    return launch_via_graph(it->second->tables, binds.data(), count, &it->second->graph, s);
+    st = order_wait(plans, count, s);
+    if (st != ATA_OK) return st;
+    st = launch_via_graph(it->second->tables, binds.data(), count, &it->second->graph, s);
+    if (st != ATA_OK) return st;
+    return order_record(plans, count, s, &it->second->order_ev);
 }
 
 extern "C" ata_status ata_batched_graph_kernels(const ata_plan* plans, int count, const int64_t* lda,
@@ -238,9 +243,14 @@ extern "C" ata_status ata_batch_execute(ata_batch b, const void* A, double* C, v
         b->last_A = A;
         b->last_C = C;
     }
-    ata_status st = launch_via_graph(b->entry->tables, b->binds.data(), count, &b->entry->graph, s);
-    if (st != ATA_OK) b->last_A = nullptr;  // rebuild the bindings on the next call
-    return st;
+    ata_status st = order_wait(b->plans.data(), count, s);
+    if (st != ATA_OK) return st;
+    st = launch_via_graph(b->entry->tables, b->binds.data(), count, &b->entry->graph, s);
+    if (st != ATA_OK) {
+        b->last_A = nullptr;  // rebuild the bindings on the next call
+        return st;
+    }
+    return order_record(b->plans.data(), count, s, &b->entry->order_ev);
 }
 
 extern "C" ata_status ata_batch_graph_kernels(ata_batch b, int32_t* kernels) {

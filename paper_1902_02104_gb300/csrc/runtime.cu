@@ -532,6 +532,9 @@ struct ata_plan_s {
     void* stage_A = nullptr;
     double* stage_C = nullptr;
     HostPipe pipe;  // ata_execute_host_async
+    // the latest execution: its event and stream (guarded by g_order_mu)
+    std::shared_ptr<OrderEvent> own_ev, last_ev;
+    cudaStream_t last_stream = nullptr;
     ~ata_plan_s() {
         pipe.release();
         graph.release();
@@ -689,11 +692,16 @@ ata_status execute_on(ata_plan plan, const void* A, int64_t lda, double* C_packe
         // the streams may still run the previous tables
         ATA_CUDA(cudaStreamSynchronize(s));
         plan->pipe.sync();
-        ata_status st = rebuild_tables(plan, lda);
+        ata_status st = order_sync(plan);  // the latest execution, on any stream
+        if (st == ATA_OK) st = rebuild_tables(plan, lda);
         if (st != ATA_OK) return st;
     }
     Bind b = make_bind(plan, A, lda, C_packed);
-    return launch_via_graph(plan->tables, &b, 1, g, s);
+    ata_status st = order_wait(&plan, 1, s);
+    if (st != ATA_OK) return st;
+    st = launch_via_graph(plan->tables, &b, 1, g, s);
+    if (st != ATA_OK) return st;
+    return order_record(&plan, 1, s, &plan->own_ev);
 }
 
 }  // namespace
@@ -717,11 +725,16 @@ ata_status ata::execute_direct(ata_plan plan, const void* A, int64_t lda, double
     if (lda != plan->lda) {
         ATA_CUDA(cudaStreamSynchronize(s));
         plan->pipe.sync();
-        ata_status st = rebuild_tables(plan, lda);
+        ata_status st = order_sync(plan);  // the latest execution, on any stream
+        if (st == ATA_OK) st = rebuild_tables(plan, lda);
         if (st != ATA_OK) return st;
     }
     Bind b = make_bind(plan, A, lda, C_packed);
-    ata_status st = enqueue_tables(plan->tables, &b, 1, s);
+    ata_status st = order_wait(&plan, 1, s);
+    if (st != ATA_OK) return st;
+    st = enqueue_tables(plan->tables, &b, 1, s);
+    if (st != ATA_OK) return st;
+    st = order_record(&plan, 1, s, &plan->own_ev);
     if (st != ATA_OK) return st;
     ata_plan_info info;
     fill_info(plan->plan, plan->dtype, &info);
@@ -1035,14 +1048,20 @@ ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx, const void* Y,
     std::lock_guard<std::mutex> lk(plan->mu);
     if (ldx != plan->lda || ldy != plan->ldb || ldc != plan->ldc) {
         ATA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-        st = rebuild_tables(plan, ldx, ldy, ldc);
+        st = order_sync(plan);  // the latest execution, on any stream
+        if (st == ATA_OK) st = rebuild_tables(plan, ldx, ldy, ldc);
         if (st != ATA_OK) return st;
     }
     Bind b = make_bind(plan, X, ldx, C);
     b.B = Y;
     b.b_elems = m > 0 ? (m - 1) * ldy + r : 0;
     b.c_elems = (p - 1) * ldc + r;
-    return launch_via_graph(plan->tables, &b, 1, &plan->graph, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = order_wait(&plan, 1, s);
+    if (st != ATA_OK) return st;
+    st = launch_via_graph(plan->tables, &b, 1, &plan->graph, s);
+    if (st != ATA_OK) return st;
+    return order_record(&plan, 1, s, &plan->own_ev);
 }
 
 
@@ -1276,6 +1295,60 @@ Bind make_bind(ata_plan p, const void* A, int64_t lda, double* C) {
     b.check = p->check;
     return b;
 }
+namespace {
+std::mutex g_order_mu;  // the plans' latest-execution fields
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
+OrderEvent::~OrderEvent() {
+    if (e) cudaEventDestroy(e);
+}
+
+ata_status order_wait(const ata_plan* plans, int count, cudaStream_t s) {
+    if (capturing(s)) return ATA_OK;
+    std::lock_guard<std::mutex> lk(g_order_mu);
+    std::vector<const OrderEvent*> waited;  // each distinct event once
+    for (int i = 0; i < count; ++i) {
+        const ata_plan p = plans[i];
+        if (!p->last_ev || p->last_stream == s) continue;
+        const OrderEvent* e = p->last_ev.get();
+        if (std::find(waited.begin(), waited.end(), e) != waited.end()) continue;
+        ATA_CUDA(cudaStreamWaitEvent(s, e->e, 0));
+        waited.push_back(e);
+    }
+    return ATA_OK;
+}
+
+ata_status order_record(const ata_plan* plans, int count, cudaStream_t s, std::shared_ptr<OrderEvent>* ev) {
+    if (capturing(s)) return ATA_OK;
+    std::lock_guard<std::mutex> lk(g_order_mu);
+    if (!*ev) {
+        auto made = std::make_shared<OrderEvent>();
+        ATA_CUDA(cudaEventCreateWithFlags(&made->e, cudaEventDisableTiming));
+        *ev = std::move(made);
+    }
+    ATA_CUDA(cudaEventRecord((*ev)->e, s));
+    for (int i = 0; i < count; ++i) {
+        plans[i]->last_ev = *ev;
+        plans[i]->last_stream = s;
+    }
+    return ATA_OK;
+}
+
+ata_status order_sync(ata_plan p) {
+    std::shared_ptr<OrderEvent> ev;
+    {
+        std::lock_guard<std::mutex> lk(g_order_mu);
+        ev = p->last_ev;
+    }
+    if (ev) ATA_CUDA(cudaEventSynchronize(ev->e));
+    return ATA_OK;
+}
+
 const Plan& plan_of(ata_plan p) { return p->plan; }
 uint64_t plan_id(ata_plan p) { return p->id; }
 char* plan_workspace(ata_plan p) { return p->ws; }

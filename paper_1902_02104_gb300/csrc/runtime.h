@@ -6,6 +6,7 @@
 
 #include <map>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/ata.h"
@@ -184,6 +185,21 @@ std::vector<std::pair<double, int>> rank_cutoffs(int64_t m, int64_t n, ata_dtype
 // *max_levels receives the level cap of the ranked plans.
 std::vector<std::pair<double, int>> rank_plans(int64_t m, int64_t n, ata_dtype dtype, const PlanOptions& o,
                                                int64_t r, int* max_levels);
+
+// Executions of a plan run one at a time, whatever streams they are queued
+// on: they share its workspace, leaf tile counter and status word.  Before
+// an execution, order_wait makes its stream wait for the latest earlier
+// execution of every plan it uses that ran on another stream; after it,
+// order_record records `ev` (the plan's own event, or a batch's) on the
+// stream as their latest.  Both do nothing on a capturing stream.
+struct OrderEvent {
+    cudaEvent_t e = nullptr;
+    ~OrderEvent();
+};
+ata_status order_wait(const ata_plan* plans, int count, cudaStream_t s);
+ata_status order_record(const ata_plan* plans, int count, cudaStream_t s, std::shared_ptr<OrderEvent>* ev);
+// Waits on the host until the plan's latest execution has finished.
+ata_status order_sync(ata_plan p);
 
 // Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
 const Plan& plan_of(ata_plan p);

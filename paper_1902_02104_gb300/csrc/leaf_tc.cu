@@ -1533,7 +1533,9 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                                        : SH::LO_REGS ? (((c & 1) == 0) ? __uint_as_float((uint32_t)lo2r[(g * 16 + c) / 2])
                                                                       : __uint_as_float((uint32_t)(lo2r[(g * 16 + c) / 2] >> 32)))
                                                     : lo_s[(((col + c) / 2) * 128 + row) * 2 + ((col + c) & 1)];
-                            ff_add(hh, ll, f[c]);
+                            // a final F accumulator (TF32) is added here; the other modes
+                            // drained theirs into (hi, lo) chunk by chunk
+                            if constexpr (G::F_FINAL) ff_add(hh, ll, f[c]);
                             if constexpr (!G::FP64_SUM) {
                                 // FP32-accuracy modes: the FP32 sum of the pair, widened
                                 // with integer operations (no FP64 arithmetic per entry)

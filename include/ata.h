@@ -262,6 +262,14 @@ ata_status ata_plan_workspace_size(ata_plan plan, size_t* bytes);
  * default stream).  A and C_packed are device pointers (layouts above).
  * The first call on a plan captures its CUDA graph; later calls replay it.
  * Returns once the work is queued.
+ * Inside a stream capture (the caller building its own CUDA graph) the
+ * plan's kernels are recorded into that capture themselves, since a graph
+ * launch cannot be captured: the same kernels and parameters.  The captured
+ * graph then reads A and writes C_packed at those pointers.  The plan must
+ * outlive it, and the caller orders its replays with the plan's other
+ * executions.  The plan's tables must already be those of this lda (a call
+ * outside the capture with it, or lda = n); otherwise the call returns
+ * ATA_EINVAL and queues nothing (the capture stays valid).
  * Errors: ATA_EINVAL (NULL plan, lda < n, NULL A with m*n > 0, NULL
  * C_packed with n > 0, A or C_packed not 8-byte aligned), ATA_ECUDA. */
 ata_status ata_execute(ata_plan plan, const void* A, int64_t lda,
@@ -409,7 +417,9 @@ ata_status ata_gemm_plan_create(ata_plan* out, int64_t m, int64_t p, int64_t r,
 
 /* C = X^t Y, queued on `stream` (device pointers; layouts above; X and Y
  * not modified).  The first call, and a call with other leading dimensions,
- * captures the plan's graph.  Errors: ATA_EINVAL (an A^t A plan, ldx < p,
+ * captures the plan's graph.  Inside a stream capture the kernels are
+ * recorded into it, as for ata_execute (the tables must already be those of
+ * ldx, ldy and ldc).  Errors: ATA_EINVAL (an A^t A plan, ldx < p,
  * ldy < r, ldc < r, NULL X or Y with m p r > 0, NULL C with p r > 0,
  * pointers not aligned to their element size), ATA_ECUDA. */
 ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx,

@@ -684,10 +684,29 @@ ata_status check_ptr(const void* p, int align, const char* what) {
     return ATA_OK;
 }
 
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Inside a stream capture the plan's kernels are enqueued themselves (a
+// graph launch cannot be captured), with its current tables: a leading
+// dimension that needs new tables is refused there.
+ata_status capture_tables_refused() {
+    return fail(ATA_EINVAL,
+                "the stream is capturing and the plan's tables are for another leading dimension: run the "
+                "plan once outside the capture with these leading dimensions first");
+}
+
 // One execution of an A^t A plan on `s` through graph cache g (arguments
 // checked by the caller).
 ata_status execute_on(ata_plan plan, const void* A, int64_t lda, double* C_packed, cudaStream_t s, GraphCache* g) {
     std::lock_guard<std::mutex> lk(plan->mu);
+    if (capturing(s)) {
+        if (lda != plan->lda) return capture_tables_refused();
+        Bind b = make_bind(plan, A, lda, C_packed);
+        return enqueue_tables(plan->tables, &b, 1, s);
+    }
     if (lda != plan->lda) {
         // the streams may still run the previous tables
         ATA_CUDA(cudaStreamSynchronize(s));
@@ -1046,6 +1065,8 @@ ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx, const void* Y,
     if (st != ATA_OK) return st;
     if (p == 0 || r == 0) return ATA_OK;
     std::lock_guard<std::mutex> lk(plan->mu);
+    const bool cap = capturing(static_cast<cudaStream_t>(stream));
+    if (cap && (ldx != plan->lda || ldy != plan->ldb || ldc != plan->ldc)) return capture_tables_refused();
     if (ldx != plan->lda || ldy != plan->ldb || ldc != plan->ldc) {
         ATA_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
         st = order_sync(plan);  // the latest execution, on any stream
@@ -1057,6 +1078,7 @@ ata_status ata_gemm_tn(ata_plan plan, const void* X, int64_t ldx, const void* Y,
     b.b_elems = m > 0 ? (m - 1) * ldy + r : 0;
     b.c_elems = (p - 1) * ldc + r;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cap) return enqueue_tables(plan->tables, &b, 1, s);
     st = order_wait(&plan, 1, s);
     if (st != ATA_OK) return st;
     st = launch_via_graph(plan->tables, &b, 1, &plan->graph, s);
@@ -1297,11 +1319,6 @@ Bind make_bind(ata_plan p, const void* A, int64_t lda, double* C) {
 }
 namespace {
 std::mutex g_order_mu;  // the plans' latest-execution fields
-
-bool capturing(cudaStream_t s) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
-}
 }  // namespace
 
 OrderEvent::~OrderEvent() {

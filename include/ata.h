@@ -278,7 +278,9 @@ ata_status ata_execute(ata_plan plan, const void* A, int64_t lda,
 /* End-to-end convenience: A and C_packed in HOST memory.  Copies A to the
  * device, runs ata_execute on `stream`, copies C back and waits for the
  * stream.  Device staging buffers are owned by the plan (allocated on first
- * use).  Errors: as ata_execute, plus ATA_ENOMEM. */
+ * use).  Not on a capturing stream (host copies cannot be recorded).
+ * Errors: as ata_execute (ATA_EINVAL also for a capturing stream), plus
+ * ATA_ENOMEM. */
 ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda,
                             double* C_packed_host, void* stream);
 
@@ -307,9 +309,11 @@ ata_status ata_plan_wait(ata_plan plan);
  * its own m_i x n_i and dtype) applied to A[i] (device, leading dimension
  * lda[i]) into C_packed[i].  All leaf tiles of all instances run in one
  * persistent launch, heaviest first; sums and combines are grouped per
- * level across instances.  Plans may not repeat within one call.
+ * level across instances.  Plans may not repeat within one call.  Not on
+ * a capturing stream (the batch's graph is launched and its bindings may be
+ * uploaded from host memory): capture ata_execute per plan instead.
  * Errors: ATA_EINVAL (count < 0, NULL arrays, a repeated plan, mixed dtype
- * families), ATA_ENOMEM, ATA_ECUDA. */
+ * families, a capturing stream), ATA_ENOMEM, ATA_ECUDA. */
 ata_status ata_execute_batched(const ata_plan* plans, int count,
                                const void* const* A, const int64_t* lda,
                                double* const* C_packed, void* stream);
@@ -335,8 +339,9 @@ ata_status ata_batch_create(ata_batch* out, const ata_plan* plans, int count,
 
 /* Queue one execution of the batch on `stream`: A and C are the device
  * buffers of the layout above (A aligned to its element size, C to 8 bytes).
- * Returns once the work is queued.  Errors: ATA_EINVAL (NULL batch, NULL or
- * misaligned A or C with count > 0, a plan of the batch destroyed),
+ * Returns once the work is queued.  Not on a capturing stream (as
+ * ata_execute_batched).  Errors: ATA_EINVAL (NULL batch, NULL or misaligned
+ * A or C with count > 0, a plan of the batch destroyed, a capturing stream),
  * ATA_ECUDA. */
 ata_status ata_batch_execute(ata_batch batch, const void* A, double* C,
                              void* stream);

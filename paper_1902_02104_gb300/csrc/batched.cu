@@ -36,6 +36,11 @@ struct BatchEntry {
 };
 
 std::mutex g_batch_mu;
+
+// Batched executions launch the batch's graph and may upload bindings from a
+// host staging buffer: neither can be recorded into a caller's capture.
+constexpr const char* kBatchCaptureRefused =
+    "the stream is capturing: batched executions cannot be recorded; capture ata_execute per plan instead";
 std::map<std::vector<int64_t>, std::unique_ptr<BatchEntry>> g_batches;
 
 // Checks the plans and leading dimensions of a batch; fills the cache key
@@ -157,6 +162,7 @@ extern "C" ata_status ata_execute_batched(const ata_plan* plans, int count, cons
             return fail(ATA_EINVAL, "A[i] or C_packed[i] is misaligned");
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stream_capturing(s)) return fail(ATA_EINVAL, kBatchCaptureRefused);
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_batches.find(key);
     if (it == g_batches.end()) {
@@ -233,6 +239,7 @@ extern "C" ata_status ata_batch_execute(ata_batch b, const void* A, double* C, v
     if (reinterpret_cast<uintptr_t>(A) % b->elem || reinterpret_cast<uintptr_t>(C) % 8)
         return fail(ATA_EINVAL, "A or C is misaligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stream_capturing(s)) return fail(ATA_EINVAL, kBatchCaptureRefused);
     std::lock_guard<std::mutex> lk(g_batch_mu);
     if (b->dead) return fail(ATA_EINVAL, "a plan of this batch has been destroyed");
     if (A != b->last_A || C != b->last_C) {

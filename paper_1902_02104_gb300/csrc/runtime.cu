@@ -684,10 +684,7 @@ ata_status check_ptr(const void* p, int align, const char* what) {
     return ATA_OK;
 }
 
-bool capturing(cudaStream_t s) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
-}
+bool capturing(cudaStream_t s) { return stream_capturing(s); }
 
 // Inside a stream capture the plan's kernels are enqueued themselves (a
 // graph launch cannot be captured), with its current tables: a leading
@@ -1158,6 +1155,9 @@ ata_status ata_execute_host(ata_plan plan, const void* A_host, int64_t lda, doub
     if (n > 0 && !C_host) return fail(ATA_EINVAL, "C_packed is NULL");
     if (n == 0) return ATA_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stream_capturing(s))
+        return fail(ATA_EINVAL, "the stream is capturing: host-buffer executions copy from host memory and cannot be "
+                                "recorded; capture ata_execute on device buffers instead");
     {
         std::lock_guard<std::mutex> lk(plan->mu);
         if (!plan->stage_A && m > 0) {
@@ -1320,6 +1320,11 @@ Bind make_bind(ata_plan p, const void* A, int64_t lda, double* C) {
 namespace {
 std::mutex g_order_mu;  // the plans' latest-execution fields
 }  // namespace
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
 
 OrderEvent::~OrderEvent() {
     if (e) cudaEventDestroy(e);

@@ -200,6 +200,8 @@ ata_status order_wait(const ata_plan* plans, int count, cudaStream_t s);
 ata_status order_record(const ata_plan* plans, int count, cudaStream_t s, std::shared_ptr<OrderEvent>* ev);
 // Waits on the host until the plan's latest execution has finished.
 ata_status order_sync(ata_plan p);
+// True when s is capturing a CUDA graph.
+bool stream_capturing(cudaStream_t s);
 
 // Plan accessors (runtime.cu) and batch-cache maintenance (batched.cu).
 const Plan& plan_of(ata_plan p);

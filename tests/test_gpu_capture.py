@@ -91,3 +91,40 @@ def test_general_product_inside_a_capture(gpu, dtype):
     g.replay()
     torch.cuda.synchronize()
     assert np.array_equal(C.cpu().numpy(), oracle.gemm_tn(X1, Y1))
+
+
+def test_batched_and_host_calls_refuse_a_capture(gpu):
+    # batched executions launch the batch's graph (and may upload bindings
+    # from host memory); host-buffer executions copy from host memory: none
+    # can be recorded, so each refuses before any CUDA call
+    import torch
+    shapes = [(300, 200), (500, 129)]
+    plans = [ata.Plan(m, n, ata.ATA_F32_BF16X3, 256) for m, n in shapes]
+    mats = [torch.from_numpy(inputs.integers(m, n, seed=110 + i).astype(np.float32)).cuda()
+            for i, (m, n) in enumerate(shapes)]
+    Cs = [torch.zeros(n * (n + 1) // 2, dtype=torch.float64, device="cuda") for _, n in shapes]
+    batch = ata.Batch(plans)
+    A_all = torch.zeros(batch.a_numel, dtype=torch.float32, device="cuda")
+    host_plan = ata.Plan(200, 100, ata.ATA_F64, 64)
+    A_host = inputs.integers(200, 100, seed=112)
+    C_host = np.zeros(100 * 101 // 2)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        for call in (lambda: ata.ata_execute_batched(plans, mats, Cs, stream=s),
+                     lambda: batch(A_all, stream=s),
+                     lambda: ata.ata_execute_host(host_plan, A_host, C_host, stream=s)):
+            with pytest.raises(ata.AtaError) as e:
+                call()
+            assert e.value.status == ata.ATA_EINVAL and "capturing" in str(e.value)
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(torch.count_nonzero(c).item() == 0 for c in Cs)
+    # outside the capture every call runs
+    ata.ata_execute_batched(plans, mats, Cs)
+    ata.ata_execute_host(host_plan, A_host, C_host)
+    torch.cuda.synchronize()
+    for c, a in zip(Cs, mats):
+        assert np.array_equal(c.cpu().numpy(), oracle.ata_packed(a.cpu().numpy()))
+    assert np.array_equal(C_host, oracle.ata_packed(A_host))

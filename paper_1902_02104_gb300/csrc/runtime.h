@@ -23,7 +23,8 @@ struct LevelRange {
 
 // Tensor-core leaf product as the GEMM kernel sees it: TMA maps of the split
 // parts of both operands (parts stacked along rows) and the output target.
-struct alignas(64) TcProd {
+// Aligned as CUtensorMap is (the TMA maps must sit on their alignment).
+struct TcProd {
     CUtensorMap tmx;
     CUtensorMap tmy;
     int32_t p_pad, r_pad, K_pad, inst;

@@ -1833,11 +1833,28 @@ void leaf_schedule(const HostTables& h, int nw, std::vector<LeafTile>* sched, st
         l.first += cost[i];
         heap.push(l);
     }
+    // Where tile lengths spread widely (batched instances: 4x or more), each
+    // worker runs its tiles alternately from the long and the short end of
+    // its list: a short tile's last drain and output then overlap the next
+    // (long) tile's MMAs through the double-buffered accumulators, instead of
+    // short tiles queueing behind one another's epilogues at the end (batched
+    // step 1.072 -> 1.057 ms).  Tiles of similar length keep the longest-first
+    // order, whose concurrent tiles share operand blocks in L2 (interleaving
+    // them cost 0.3%).  The workers' loads are the assignment's either way.
+    const bool interleave = ntiles > 0 && cost[idx.front()] >= 4 * cost[idx.back()];
     sched->clear();
     wfirst->assign(nw + 1, 0);
     for (int w = 0; w < nw; ++w) {
         (*wfirst)[w] = (int32_t)sched->size();
-        for (int i : lists[w]) sched->push_back(h.tiles[i]);
+        const std::vector<int>& l = lists[w];  // longest first
+        if (!interleave) {
+            for (int i : l) sched->push_back(h.tiles[i]);
+            continue;
+        }
+        for (size_t a = 0, b = l.size(); a < b;) {
+            sched->push_back(h.tiles[l[a++]]);
+            if (a < b) sched->push_back(h.tiles[l[--b]]);
+        }
     }
     (*wfirst)[nw] = (int32_t)sched->size();
 }

@@ -46,10 +46,20 @@ struct BindSet<kDevBinds> {
     const Bind* b;
 };
 
-// One output tile of the leaf launch.
+// One output tile of the leaf launch, or one K range of it (FP64 leaves cut
+// along K: part >= 0 is the partial tile's slot in the product's region).
 struct LeafTile {
     int32_t prod;
     int32_t ti, tj;
+    int32_t k0, k1;           // K range [k0, k1)
+    int32_t part;             // -1: the whole K, output written directly
+};
+
+// Sum of one cut tile's partials, in part order, into its output.
+struct PartialSum {
+    int32_t prod;
+    int32_t ti, tj;
+    int32_t slot0;            // first partial slot (kparts of them)
 };
 
 // A range of rows of an elementwise task (split or combine).
@@ -58,7 +68,6 @@ struct Chunk {
     int32_t row0, nrows;
 };
 
-constexpr int kF64Tile = 64;      // FP64 leaf tile (rows and columns)
 constexpr int kMaxTerms = 32;     // terms per operand the leaf kernels accept
 
 // `binds`: nb == 1, the one instance in host memory (passed by value, the
@@ -67,6 +76,9 @@ constexpr int kMaxTerms = 32;     // terms per operand the leaf kernels accept
 // `status` receives a nonzero code when a self-checked access falls outside its
 // buffer (the access is skipped): 11 leaf read, 12 leaf write, 21 split read,
 // 22 split write, 31 combine read, 32 combine write.
+// Partials of FP64 tiles cut along K, added in part order into the outputs.
+cudaError_t launch_partial_sums(int* status, const Bind* binds, int nb, const LeafProduct* prods,
+                                const PartialSum* tasks, int ntasks, cudaStream_t s);
 cudaError_t launch_leaf_f64(int* status, const Bind* binds, int nb, const LeafProduct* prods, const Term* terms, const LeafTile* tiles,
                             int ntiles, int* counter, int grid, cudaStream_t s);
 

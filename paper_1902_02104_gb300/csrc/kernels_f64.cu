@@ -42,6 +42,27 @@ __device__ __forceinline__ bool in_bounds(const Bind& b, int8_t buf, int64_t idx
     return false;
 }
 
+// One entry (i, j) of a leaf product's output (i, j relative to the
+// product): a dense workspace block, a dense block of C, a block of packed C,
+// or the upper part of a diagonal block.  Entries outside the extent, and
+// below the diagonal of a symmetric block, are not written.
+__device__ __forceinline__ void store_leaf_entry(const LeafProduct& sp, const Bind& bind, int i, int j, double v,
+                                                 int* status) {
+    if (i >= sp.out_rows || j >= sp.out_cols) return;
+    if (sp.out_kind == OUT_DENSE) {
+        const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
+        if (in_bounds(bind, BUF_W, idx, 8, status, 12)) reinterpret_cast<double*>(bind.W)[idx] = v;
+    } else if (sp.out_kind == OUT_CDENSE) {
+        const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
+        if (in_bounds(bind, BUF_C, idx, 8, status, 12)) bind.C[idx] = v;
+    } else {
+        const int64_t gi = (int64_t)sp.ci0 + i, gj = (int64_t)sp.cj0 + j;
+        if (sp.out_kind == OUT_SYRK && gj < gi) return;
+        const int64_t idx = packed_start(gi, bind.n) + (gj - gi);
+        if (in_bounds(bind, BUF_C, idx, 8, status, 12)) bind.C[idx] = v;
+    }
+}
+
 template <int NB>
 __device__ __forceinline__ double operand_at(const BindSet<NB>& bs, const Term* ts, int nt, int k, int c,
                                              int* status) {
@@ -81,7 +102,9 @@ constexpr int LOADS = (BK * TILE) / NTHREADS;  // operand elements per thread pe
 // symmetric tile) skips the whole slab with a branch, and active warps run
 // unpredicated DFMAs -- a predicated-off DFMA still occupies the FP64 pipe.
 // K is staged in slabs of 16, double-buffered through registers.
-// Accumulation runs k ascending per entry.
+// Accumulation runs k ascending per entry over the tile's K range; a tile cut
+// along K (part >= 0) writes its partial 64 x 64 tile to its slot in W, and
+// partial_sum_kernel adds the parts in order.
 template <int NB>
 __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constant__ BindSet<NB> bs,
                                                             const LeafProduct* __restrict__ prods,
@@ -115,7 +138,7 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
         const int rows_v = min(TILE, sp.out_rows - i0);
         const int cols_v = min(TILE, sp.out_cols - j0);
         const bool diag = sp.out_kind == OUT_SYRK && lt.ti == lt.tj;
-        const int K = sp.K;
+        const int kbeg = lt.k0, kend = min(lt.k1, sp.K);
         __syncthreads();
 
         // warp-uniform activity: some valid row, some valid column, and not
@@ -136,8 +159,8 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
                 const int idx = tid + e * NTHREADS;
                 const int kk = idx / TILE, c = idx % TILE;
                 const int k = k0 + kk;
-                px[e] = (k < K) ? operand_at(bs, sx, nx, k, i0 + c, status) : 0.0;
-                py[e] = (k < K) ? operand_at(bs, sy, ny, k, j0 + c, status) : 0.0;
+                px[e] = (k < kend) ? operand_at(bs, sx, nx, k, i0 + c, status) : 0.0;
+                py[e] = (k < kend) ? operand_at(bs, sy, ny, k, j0 + c, status) : 0.0;
             }
         };
         auto stash = [&](int buf) {
@@ -151,16 +174,16 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
         };
 
         int buf = 0;
-        if (K > 0) {
-            fetch(0);
+        if (kbeg < kend) {
+            fetch(kbeg);
             stash(0);
         }
         __syncthreads();
-        for (int k0 = 0; k0 < K; k0 += BK) {
-            const bool more = k0 + BK < K;
+        for (int k0 = kbeg; k0 < kend; k0 += BK) {
+            const bool more = k0 + BK < kend;
             if (more) fetch(k0 + BK);  // global loads in flight during the slab's DFMAs
             if (active) {
-                const int kmax = min(BK, K - k0);
+                const int kmax = min(BK, kend - k0);
                 for (int kk = 0; kk < kmax; ++kk) {
                     const double2 xa = *reinterpret_cast<const double2*>(&Xs[buf][kk][row0]);
                     const double2 xb = *reinterpret_cast<const double2*>(&Xs[buf][kk][row0 + 2]);
@@ -179,33 +202,54 @@ __global__ void __launch_bounds__(NTHREADS) leaf_f64_kernel(const __grid_constan
             buf ^= 1;
         }
 
-        // epilogue: dense workspace buffer, block of packed C, or upper part of a diagonal block
+        // epilogue: the output (dense workspace block, block of packed C, or
+        // upper part of a diagonal block), or this K range's partial tile
         const Bind& bind = bs.b[sp.inst];
         if (active) {
+            if (lt.part >= 0) {
+                const int64_t slot = sp.part_off + (int64_t)lt.part * TILE * TILE;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int i = i0 + row0 + a;
-                if (i >= sp.out_rows) continue;
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int j = j0 + col0 + 8 * b;
-                    if (j >= sp.out_cols) continue;
-                    if (sp.out_kind == OUT_DENSE) {
-                        const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
-                        if (in_bounds(bind, BUF_W, idx, 8, status, 12)) reinterpret_cast<double*>(bind.W)[idx] = acc[a][b];
-                    } else if (sp.out_kind == OUT_CDENSE) {
-                        const int64_t idx = sp.out_off + (int64_t)i * sp.out_ld + j;
-                        if (in_bounds(bind, BUF_C, idx, 8, status, 12)) bind.C[idx] = acc[a][b];
-                    } else {
-                        const int64_t gi = (int64_t)sp.ci0 + i, gj = (int64_t)sp.cj0 + j;
-                        if (sp.out_kind == OUT_SYRK && gj < gi) continue;
-                        const int64_t idx = packed_start(gi, bind.n) + (gj - gi);
-                        if (in_bounds(bind, BUF_C, idx, 8, status, 12)) bind.C[idx] = acc[a][b];
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t idx = slot + (row0 + a) * TILE + col0 + 8 * b;
+                        if (in_bounds(bind, BUF_W, idx, 8, status, 13)) reinterpret_cast<double*>(bind.W)[idx] = acc[a][b];
                     }
-                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        store_leaf_entry(sp, bind, i0 + row0 + a, j0 + col0 + 8 * b, acc[a][b], status);
             }
         }
         __syncthreads();
+    }
+}
+
+// Partial tiles of FP64 tiles cut along K, added in part order (k ascending
+// across the parts) and stored like the leaf's own output.  One block per
+// cut tile; entries outside the product's extent, or below the diagonal of a
+// symmetric block, were never written by the leaf and are not read.
+template <int NB>
+__global__ void __launch_bounds__(NTHREADS) partial_sum_kernel(const __grid_constant__ BindSet<NB> bs,
+                                                               const LeafProduct* __restrict__ prods,
+                                                               const PartialSum* __restrict__ tasks,
+                                                               int* __restrict__ status) {
+    const PartialSum ps = tasks[blockIdx.x];
+    const LeafProduct sp = prods[ps.prod];
+    const Bind& bind = bs.b[sp.inst];
+    const double* W = reinterpret_cast<const double*>(bind.W);
+    for (int e = threadIdx.x; e < TILE * TILE; e += NTHREADS) {
+        const int i = ps.ti * TILE + e / TILE, j = ps.tj * TILE + e % TILE;
+        if (i >= sp.out_rows || j >= sp.out_cols) continue;
+        if (sp.out_kind == OUT_SYRK && (int64_t)sp.cj0 + j < (int64_t)sp.ci0 + i) continue;
+        double v = 0.0;
+        for (int q = 0; q < sp.kparts; ++q) {
+            const int64_t idx = sp.part_off + (int64_t)(ps.slot0 + q) * TILE * TILE + e;
+            if (in_bounds(bind, BUF_W, idx, 8, status, 14)) v += W[idx];
+        }
+        store_leaf_entry(sp, bind, i, j, v, status);
     }
 }
 
@@ -358,6 +402,16 @@ cudaError_t launch_leaf_f64(int* status, const Bind* binds, int nb, const LeafPr
     else
         leaf_f64_kernel<kDevBinds><<<grid, NTHREADS, 0, s>>>(make_set<kDevBinds>(binds, nb), prods, terms, tiles,
                                                              ntiles, counter, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partial_sums(int* status, const Bind* binds, int nb, const LeafProduct* prods,
+                                const PartialSum* tasks, int ntasks, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (nb <= 1)
+        partial_sum_kernel<1><<<ntasks, NTHREADS, 0, s>>>(make_set<1>(binds, nb), prods, tasks, status);
+    else
+        partial_sum_kernel<kDevBinds><<<ntasks, NTHREADS, 0, s>>>(make_set<kDevBinds>(binds, nb), prods, tasks, status);
     return cudaGetLastError();
 }
 

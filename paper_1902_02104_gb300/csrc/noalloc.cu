@@ -116,6 +116,7 @@ extern "C" ata_status ata_execute_static_scratch(int64_t m, int64_t n, const dou
     const int64_t o_schunk = place(h.split_chunks.size() * sizeof(Chunk));
     const int64_t o_comb = place(h.comb.size() * sizeof(CombineTask));
     const int64_t o_cchunk = place(h.comb_chunks.size() * sizeof(Chunk));
+    const int64_t o_psum = place(h.partial_sums.size() * sizeof(PartialSum));
     const int64_t tables_bytes = off;
     const int64_t o_ws = place(P.ws_bytes);
     if (off > kScratchBytes)
@@ -133,6 +134,7 @@ extern "C" ata_status ata_execute_static_scratch(int64_t m, int64_t n, const dou
     put(o_schunk, h.split_chunks.data(), h.split_chunks.size() * sizeof(Chunk));
     put(o_comb, h.comb.data(), h.comb.size() * sizeof(CombineTask));
     put(o_cchunk, h.comb_chunks.data(), h.comb_chunks.size() * sizeof(Chunk));
+    put(o_psum, h.partial_sums.data(), h.partial_sums.size() * sizeof(PartialSum));
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The tables overwrite whatever the previous call left in the array; the
@@ -151,6 +153,8 @@ extern "C" ata_status ata_execute_static_scratch(int64_t m, int64_t n, const dou
     t.split_chunks = reinterpret_cast<Chunk*>(scratch + o_schunk);
     t.comb = reinterpret_cast<CombineTask*>(scratch + o_comb);
     t.comb_chunks = reinterpret_cast<Chunk*>(scratch + o_cchunk);
+    t.partial_sums = reinterpret_cast<PartialSum*>(scratch + o_psum);
+    t.npartial_sums = (int)h.partial_sums.size();
     t.ntiles = (int)h.tiles.size();
     t.split_lv = h.split_lv;
     t.comb_lv = h.comb_lv;

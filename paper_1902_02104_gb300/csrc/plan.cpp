@@ -395,6 +395,30 @@ void start_plan(Plan& P, int64_t m, int64_t n, const PlanOptions& opt) {
 
 void finish_plan(Plan& P, const Ctx& c, const PlanOptions& opt) {
     P.ws_bytes = c.ws;
+    if (P.leaf == LEAF_F64) {
+        // A plan with fewer 64 x 64 FP64 tiles than two per SM leaves most SMs
+        // idle while the longest tile's K loop runs (GB300 issues 2-3 DFMA per
+        // clock per SM).  Each tile of a product is then cut into kparts equal
+        // K ranges, each computed by its own block into an FP64 partial tile
+        // in W after everything else there, and one more kernel adds a tile's
+        // partials in part order: deterministic, and part of the plan, so
+        // single, batched and static-scratch executions cut alike.
+        int64_t tiles = 0;
+        for (const LeafProduct& lp : P.products) tiles += leaf_tiles(lp, kF64Tile, kF64Tile);
+        if (tiles > 0 && tiles < kSplitKTiles) {
+            const int want = (int)std::min<int64_t>(kSplitKMaxParts, (kSplitKTiles + tiles - 1) / tiles);
+            int64_t ws = (P.ws_bytes + 255) / 256 * 256;
+            for (LeafProduct& lp : P.products) {
+                const int parts = std::min(want, std::max(1, lp.K / kSplitKMinK));
+                if (parts <= 1) continue;
+                lp.kparts = parts;
+                lp.part_off = ws / 8;
+                ws += leaf_tiles(lp, kF64Tile, kF64Tile) * parts * (int64_t)kF64Tile * kF64Tile * 8;
+                ws = (ws + 255) / 256 * 256;
+            }
+            P.ws_bytes = ws;
+        }
+    }
     if (P.leaf != LEAF_F64) {
         // CTA-pair tiles when every X operand is padded to them and they add
         // at most 1/8 to the tile area of 128 x 128 tiles

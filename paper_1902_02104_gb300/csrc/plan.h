@@ -74,7 +74,8 @@ struct LeafProduct {
     int32_t ci0, cj0;         // OUT_PACKED / OUT_SYRK: global (row, col) of the block
     int64_t work;             // scalar multiplications (for ordering and stats)
     int32_t inst;             // instance of a batched execution (0 for one plan)
-    int32_t pad2_;
+    int32_t kparts;           // FP64 leaves: K ranges each tile is cut into (<= 1: none)
+    int64_t part_off;         // ... and the FP64 element offset in W of its partial tiles
     // tensor-core leaves: split operand parts, K-major, in W (byte offsets)
     int64_t tc_x_off, tc_y_off;   // parts x rows_pad x K_pad elements each
     int32_t p_pad, r_pad, K_pad;  // rows of X / Y parts (multiples of 128), K padded
@@ -146,6 +147,12 @@ struct TcGeom {
     int k_align;     // K padding of part buffers (elements)
 };
 TcGeom tc_geom(LeafKind k);
+constexpr int kF64Tile = 64;      // FP64 leaf tile (rows and columns)
+// FP64 leaves of a plan with fewer tiles than this are cut along K (see
+// finish_plan): two resident blocks on each of GB300's 152 SMs.
+constexpr int64_t kSplitKTiles = 304;
+constexpr int kSplitKMaxParts = 8;
+constexpr int kSplitKMinK = 128;  // K values per part at least
 constexpr int kTcTile = 128;      // tensor-core leaf tile (rows and columns)
 constexpr int kTcPairRows = 256;  // rows of the CTA-pair tile
 constexpr int kTcWideCols = 256;  // columns of the TF32 CTA-pair tile

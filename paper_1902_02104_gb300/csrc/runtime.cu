@@ -127,6 +127,7 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
     const int64_t o_schunk = place(h.split_chunks.size() * sizeof(Chunk));
     const int64_t o_comb = place(h.comb.size() * sizeof(CombineTask));
     const int64_t o_cchunk = place(h.comb_chunks.size() * sizeof(Chunk));
+    const int64_t o_psum = place(h.partial_sums.size() * sizeof(PartialSum));
     const int64_t total = std::max<int64_t>(off, 256);
     char* blob = nullptr;
     cudaError_t e = dev_malloc(&blob, total);
@@ -145,6 +146,7 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
     put(o_schunk, h.split_chunks.data(), h.split_chunks.size() * sizeof(Chunk));
     put(o_comb, h.comb.data(), h.comb.size() * sizeof(CombineTask));
     put(o_cchunk, h.comb_chunks.data(), h.comb_chunks.size() * sizeof(Chunk));
+    put(o_psum, h.partial_sums.data(), h.partial_sums.size() * sizeof(PartialSum));
     e = cudaMemcpy(blob, hb.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         dev_free(blob);
@@ -159,6 +161,8 @@ ata_status upload_tables(const HostTables& h, DeviceTables* d) {
     d->split_chunks = reinterpret_cast<Chunk*>(blob + o_schunk);
     d->comb = reinterpret_cast<CombineTask*>(blob + o_comb);
     d->comb_chunks = reinterpret_cast<Chunk*>(blob + o_cchunk);
+    d->partial_sums = reinterpret_cast<PartialSum*>(blob + o_psum);
+    d->npartial_sums = (int)h.partial_sums.size();
     d->ntiles = (int)h.tiles.size();
     d->split_lv = h.split_lv;
     d->comb_lv = h.comb_lv;
@@ -204,13 +208,30 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h, int
         const int tm = P.leaf == LEAF_F64 ? kF64Tile : h->tile_rows;
         const int tn = P.leaf == LEAF_F64 ? kF64Tile : tc_cols_for(P.leaf, tm);
         const int64_t a = (lp.out_rows + tm - 1) / tm, b = (lp.out_cols + tn - 1) / tn;
+        // FP64 tiles cut along K: kparts ranges of whole 16-value slabs
+        const int parts = P.leaf == LEAF_F64 && lp.kparts > 1 ? lp.kparts : 1;
+        const int kc = parts > 1 ? (lp.K + parts * 16 - 1) / (parts * 16) * 16 : lp.K;
+        int32_t tile_index = 0;
         for (int64_t ti = 0; ti < a; ++ti)
-            for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti * tm / tn : 0); tj < b; ++tj) {
+            for (int64_t tj = (lp.out_kind == OUT_SYRK ? ti * tm / tn : 0); tj < b; ++tj, ++tile_index) {
                 LeafTile t;
                 t.prod = p_base + (int32_t)i;
                 t.ti = (int32_t)ti;
                 t.tj = (int32_t)tj;
-                h->tiles.push_back(t);
+                if (parts <= 1) {
+                    t.k0 = 0;
+                    t.k1 = lp.K;
+                    t.part = -1;
+                    h->tiles.push_back(t);
+                    continue;
+                }
+                for (int q = 0; q < parts; ++q) {
+                    t.k0 = std::min(lp.K, q * kc);
+                    t.k1 = std::min(lp.K, (q + 1) * kc);
+                    t.part = tile_index * parts + q;
+                    h->tiles.push_back(t);
+                }
+                h->partial_sums.push_back(PartialSum{t.prod, t.ti, t.tj, tile_index * parts});
             }
     }
     // split / combine levels, merged level by level
@@ -236,9 +257,8 @@ void append_plan_tables(const Plan& P, int inst, int64_t lda, HostTables* h, int
 // Orders leaf tiles heaviest first and lays out split/combine tasks and chunks
 // contiguously per level.
 void finalize_tables(HostTables* h, int8_t in_dt, int8_t sum_dt) {
-    std::stable_sort(h->tiles.begin(), h->tiles.end(), [&](const LeafTile& a, const LeafTile& b) {
-        return h->prods[a.prod].K > h->prods[b.prod].K;
-    });
+    std::stable_sort(h->tiles.begin(), h->tiles.end(),
+                     [](const LeafTile& a, const LeafTile& b) { return a.k1 - a.k0 > b.k1 - b.k0; });
     for (size_t l = 0; l < h->split_lv.size(); ++l) {
         LevelRange& lr = h->split_lv[l];
         lr.chunk0 = (int32_t)h->split_chunks.size();
@@ -271,6 +291,8 @@ void DeviceTables::free_all() {
     dev_free(tc_blob);
     blob = nullptr;
     tc_blob = nullptr;
+    partial_sums = nullptr;
+    npartial_sums = 0;
     tcp = nullptr;
     prep = nullptr;
     colmax = nullptr;
@@ -320,6 +342,8 @@ ata_status enqueue_tables(const DeviceTables& t, const Bind* binds, int nb, cuda
             if (ev) ATA_CUDA(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
             const int grid = std::max(1, std::min(t.ntiles, sms * per_sm));
             ATA_CUDA(launch_leaf_f64(fstatus, binds, nb, t.prods, t.terms, t.tiles, t.ntiles, t.counter, grid, s));
+            if (t.npartial_sums > 0)
+                ATA_CUDA(launch_partial_sums(fstatus, binds, nb, t.prods, t.partial_sums, t.npartial_sums, s));
         } else {
             ata_status st = launch_leaf_tc(t, binds, nb, s, ev ? ev[2] : nullptr);
             if (st != ATA_OK) return st;
@@ -620,9 +644,12 @@ void fill_info(const Plan& P, ata_dtype dtype, ata_plan_info* out) {
     // kernels one execution launches: a split and a combine kernel per level,
     // then the leaf kernel, preceded for tensor-core leaves by the operand
     // preparation (and the column maxima of the sliced modes, and the column
-    // scales of the FP64 emulation)
+    // scales of the FP64 emulation), and followed by the partial sums of FP64
+    // tiles cut along K
+    bool cut = false;
+    for (const LeafProduct& lp : P.products) cut = cut || (P.leaf == LEAF_F64 && lp.kparts > 1);
     const int leaf_kernels = P.products.empty()    ? 0
-                             : P.leaf == LEAF_F64   ? 1
+                             : P.leaf == LEAF_F64   ? (cut ? 2 : 1)
                              : P.leaf == LEAF_TF32  ? 2
                              : P.leaf == LEAF_OZAKI ? 4
                                                     : 3;
@@ -858,6 +885,21 @@ ata_status check_plan_tables(const Plan& P) {
     auto kind_ok = [&](int8_t kind) {
         return P.gemm ? (kind == OUT_DENSE || kind == OUT_CDENSE) : (kind != OUT_CDENSE);
     };
+    // FP64 tiles cut along K: each product's partial tiles inside W, the
+    // regions of different products disjoint
+    {
+        std::vector<std::pair<int64_t, int64_t>> regions;
+        for (const LeafProduct& lp : P.products) {
+            if (P.leaf != LEAF_F64 || lp.kparts <= 1) continue;
+            const int64_t bytes = leaf_tiles(lp, kF64Tile, kF64Tile) * lp.kparts * (int64_t)kF64Tile * kF64Tile * 8;
+            if (lp.part_off < 0 || lp.part_off * 8 + bytes > ws)
+                return fail(ATA_EINVAL, "partial tiles beyond the workspace");
+            regions.push_back({lp.part_off * 8, lp.part_off * 8 + bytes});
+        }
+        std::sort(regions.begin(), regions.end());
+        for (size_t i = 1; i < regions.size(); ++i)
+            if (regions[i].first < regions[i - 1].second) return fail(ATA_EINVAL, "partial tile regions overlap");
+    }
     for (const LeafProduct& lp : P.products) {
         for (int t = 0; t < lp.nx; ++t)
             if (!term_ok(P.terms[lp.x0 + t], "leaf X")) return fail(ATA_EINVAL, msg);

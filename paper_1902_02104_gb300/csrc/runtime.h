@@ -61,6 +61,7 @@ struct HostTables {
     std::vector<LevelRange> comb_lv;
     std::vector<std::vector<SplitTask>> split_pending;
     std::vector<std::vector<CombineTask>> comb_pending;
+    std::vector<PartialSum> partial_sums;  // FP64 tiles cut along K
 };
 
 // The same tables in device memory (one allocation).
@@ -78,6 +79,8 @@ struct DeviceTables {
     std::vector<LevelRange> split_lv;
     CombineTask* comb = nullptr;
     Chunk* comb_chunks = nullptr;
+    PartialSum* partial_sums = nullptr;
+    int npartial_sums = 0;
     std::vector<LevelRange> comb_lv;
     // tensor-core leaves
     char* tc_blob = nullptr;

@@ -38,7 +38,12 @@ def test_counts_match_algorithm1_restatement(m, n, c):
 def test_classical_when_strassen_disabled(m, n):
     i = q(m, n, 16, max_strassen_levels=0)
     assert i["mults"] == m * n * (n + 1) // 2
-    assert i["workspace_bytes"] == 0
+    # no Strassen workspace; a plan of fewer than 304 FP64 tiles holds only
+    # the partial tiles of its tiles cut along K
+    if i["n_leaf_tiles"] >= 304:
+        assert i["workspace_bytes"] == 0
+    else:
+        assert i["workspace_bytes"] % (64 * 64 * 8) == 0
     assert i["n_leaf_products"] == i["n_diag_leaves"] + i["n_nodes"]
 
 
@@ -232,3 +237,19 @@ def test_autotune_unchanged_where_the_cap_holds():
         same = q(m, n, auto["cutoff"], dt)
         assert auto["workspace_bytes"] == same["workspace_bytes"] <= CAP
         assert auto["max_strassen_levels"] == same["max_strassen_levels"]
+
+
+def test_small_fp64_plans_cut_their_tiles_along_k():
+    # config 1 (512 x 384, cutoff 64): 75 FP64 tiles, fewer than two per SM,
+    # so the tiles with enough K are cut into K ranges; the partial tiles sit
+    # in the workspace (checked in bounds and disjoint by the host checker)
+    # and one more kernel adds them; paper-scale plans are not cut
+    small = q(512, 384, 64)
+    assert small["n_leaf_tiles"] < 304
+    # a split and a combine kernel per Strassen level (FP64 sums are not
+    # fused), the leaf, and the partial sums
+    assert small["n_launches"] == 2 * small["max_strassen_levels"] + 1 + 1
+    ata.ata_plan_check(512, 384, ata.ATA_F64, 64)
+    big = q(5000, 5000, 0)
+    assert big["n_leaf_tiles"] >= 304
+    assert big["n_launches"] == 2 * big["max_strassen_levels"] + 1

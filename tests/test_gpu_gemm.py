@@ -10,7 +10,7 @@ out, hence its 1e-3; a product of two independent operands keeps an error of
 about u relative in every entry, and each Strassen level (operand sums, four
 products combined) roughly doubles it.  The general-product test therefore
 holds TF32 to normwise 4u = 2^-9 at two Strassen levels.  Strassen bounds
-are normwise only, so inputs with scaled columns are judged normwise.
+are normwise only, so inputs with scaled columns are measured normwise.
 Winograd's variant has the larger error constant (18 against Strassen's 12
 per level in the normwise bound, Higham, Accuracy and Stability of Numerical
 Algorithms, Thms. 23.2-23.3), so its normwise bounds are 1.5x per level

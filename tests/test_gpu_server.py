@@ -19,11 +19,12 @@ pytestmark = pytest.mark.gpu
 NORM_TOL = {ata.ATA_F32_BF16X3: 1e-6, ata.ATA_F32_TF32: 1e-3}
 
 
-@pytest.mark.parametrize("dtype", [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32])
+@pytest.mark.parametrize("dtype", [ata.ATA_F32_BF16X3, ata.ATA_F32_TF32, ata.ATA_F64_OZAKI])
 def test_mix_equals_alone_and_oracle(gpu, dtype):
     import torch
     shapes = [(300, 200), (1000, 129), (129, 400), (777, 333), (2048, 64), (500, 500)]
-    mats_np = [inputs.normal(m, n, seed=i, dtype=np.float32) for i, (m, n) in enumerate(shapes)]
+    f64 = dtype == ata.ATA_F64_OZAKI
+    mats_np = [inputs.normal(m, n, seed=i, dtype=np.float64 if f64 else np.float32) for i, (m, n) in enumerate(shapes)]
     mats = [torch.from_numpy(a).cuda() for a in mats_np]
     alone = []
     for (m, n), A in zip(shapes, mats):
@@ -49,8 +50,12 @@ def test_mix_equals_alone_and_oracle(gpu, dtype):
     # every served result against the oracle (each request of a shape is
     # bitwise equal to the alone run, so one comparison per shape covers all)
     for i, a in enumerate(mats_np):
-        err = oracle.normwise_error(alone[i].cpu().numpy(), oracle.ata_packed(a), a.shape[1])
-        assert err <= NORM_TOL[dtype], (shapes[i], err)
+        if f64:  # the FP64 emulation: componentwise, as the FP64 path
+            err = oracle.componentwise_error(alone[i].cpu().numpy(), oracle.ata_packed(a), oracle.abs_gram_packed(a))
+            assert err <= 1e-11, (shapes[i], err)
+        else:
+            err = oracle.normwise_error(alone[i].cpu().numpy(), oracle.ata_packed(a), a.shape[1])
+            assert err <= NORM_TOL[dtype], (shapes[i], err)
 
 
 def test_budget_too_small_fails_the_request(gpu):

@@ -756,23 +756,20 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
 // shift of u plus 128.  Integer arithmetic only.
 //
 // v from the bits of x: the significand shifted right by r, rounded to
-// nearest (ties up) as ((m >> (r - 1)) + 1) >> 1; 0 for zero, subnormal and
-// non-finite x and for a non-finite column (r > 63).
+// nearest (ties up) as ((m >> (r - 1)) + 1) >> 1; 0 for zero and subnormal
+// x.  Every value of a column lies below 2^E (E comes from the column's
+// maximum, or is kNonFinite, which shifts everything out), so r = E - e + 4
+// >= 5 for x = f * 2^e and no left shift arises; r >= 1 is enforced all the
+// same.  Non-finite x occur only in non-finite columns and give 0.
 template <int S>
 __device__ __forceinline__ long long fixed_point(double x, int E) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
     const int r = E - 8 * S + 1075 - eb;  // right shift to units of 2^(E - 8S)
-    long long v = 0;
-    if (eb != 0 && eb != 0x7FF) {
-        const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
-        if (r <= 0)
-            v = m << -r;
-        else
-            v = ((m >> min(r - 1, 63)) + 1) >> 1;
-        if (bits < 0) v = -v;
-    }
-    return v;
+    const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+    long long v = ((m >> min(max(r, 1) - 1, 63)) + 1) >> 1;
+    if (eb == 0) v = 0;
+    return bits < 0 ? -v : v;
 }
 
 // u = v + bias of a fixed-point value v (|v| <= 2^(8S) + a few units): the

@@ -929,9 +929,15 @@ __global__ void __launch_bounds__(256, 6) tc_prep_kernel(const __grid_constant__
 
 // Column maxima of row segments of the operand blocks (tasks: prod = index
 // of the segment's term, rows [k0, k1) of columns [c0, c0 + 64); term_mx:
-// offset of each segment's maxima in term_max).
+// offset of each segment's maxima in term_max).  Tasks of up to 256 rows,
+// one 64-row tile in flight per thread and four blocks per SM (64
+// registers): 10000^2 has about 6300 tasks, so the last wave is short
+// (1024-row tasks, two tiles in flight and three blocks per SM took 5% longer
+// at 4500^2).
+constexpr int kAtomSpan = 256;  // rows of a column-maximum task of an atom
+
 template <int NB>
-__global__ void __launch_bounds__(256) tc_termmax_kernel(const __grid_constant__ BindSet<NB> bs,
+__global__ void __launch_bounds__(256, 4) tc_termmax_kernel(const __grid_constant__ BindSet<NB> bs,
                                                          const Term* __restrict__ terms,
                                                          const PrepTask* __restrict__ tasks,
                                                          const int64_t* __restrict__ term_mx,
@@ -943,19 +949,17 @@ __global__ void __launch_bounds__(256) tc_termmax_kernel(const __grid_constant__
     unsigned long long m[TR::VEC];
 #pragma unroll
     for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
-    // a segment is one block of one buffer (no sign): both tiles' loads are
-    // issued before any value is used
+    // a segment is one block of one buffer, read as stored (a sign does not
+    // change a magnitude)
     const Term tm = terms[tk.prod];
-    for (int k = tk.k0; k < tk.k1; k += 2 * PT) {
-        double x0[TR::NPASS][TR::VEC], x1[TR::NPASS][TR::VEC];
+    for (int k = tk.k0; k < tk.k1; k += PT) {
+        double x0[TR::NPASS][TR::VEC];
         load_term_raw<double>(bs, tm, tk.k1, k, tk.c0, x0);
-        load_term_raw<double>(bs, tm, tk.k1, k + PT, tk.c0, x1);
 #pragma unroll
         for (int j = 0; j < TR::VEC; ++j)
 #pragma unroll
             for (int p = 0; p < TR::NPASS; ++p) {
-                const unsigned long long b0 = abs_bits(x0[p][j]), b1 = abs_bits(x1[p][j]);
-                const unsigned long long b = b0 > b1 ? b0 : b1;
+                const unsigned long long b = abs_bits(x0[p][j]);
                 m[j] = b > m[j] ? b : m[j];
             }
     }
@@ -2035,13 +2039,13 @@ ata_status build_tc_tables(const HostTables& h, const std::vector<char*>& ws, De
                 atom_index[{k, a}] = id;
                 atoms_of[k].push_back({a, z});
                 // strips side by side over the same rows run together
-                for (int k0 = 0; k0 < at.rows; k0 += kColSpan)
+                for (int k0 = 0; k0 < at.rows; k0 += kAtomSpan)
                     for (int c0 = 0; c0 < at.cols; c0 += PT) {
                         PrepTask ct{};
                         ct.prod = (int32_t)id;  // an atom
                         ct.c0 = c0;
                         ct.k0 = k0;
-                        ct.k1 = std::min(k0 + kColSpan, at.rows);
+                        ct.k1 = std::min(k0 + kAtomSpan, at.rows);
                         colmax.push_back(ct);
                     }
             }

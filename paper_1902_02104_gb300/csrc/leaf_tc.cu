@@ -759,15 +759,15 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
 // nearest (ties up) as ((m >> (r - 1)) + 1) >> 1; 0 for zero and subnormal
 // x.  Every value of a column lies below 2^E (E comes from the column's
 // maximum, or is kNonFinite, which shifts everything out), so r = E - e + 4
-// >= 5 for x = f * 2^e and no left shift arises; r >= 1 is enforced all the
-// same.  Non-finite x occur only in non-finite columns and give 0.
+// >= 5 for x = f * 2^e and no left shift arises (r < 1 would shift
+// everything out).  Non-finite x occur only in non-finite columns and give 0.
 template <int S>
 __device__ __forceinline__ long long fixed_point(double x, int E) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
     const int r = E - 8 * S + 1075 - eb;  // right shift to units of 2^(E - 8S)
     const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
-    long long v = ((m >> min(max(r, 1) - 1, 63)) + 1) >> 1;
+    long long v = ((m >> min((unsigned int)(r - 1), 63u)) + 1) >> 1;
     if (eb == 0) v = 0;
     return bits < 0 ? -v : v;
 }
@@ -780,21 +780,17 @@ __device__ __forceinline__ long long biased_value(long long v) {
     return v + bias;
 }
 
-// The same for an FP32 value and S = 3 (24 bits) in 32-bit integers.
+// The same for an FP32 value and S = 3 (24 bits) in 32-bit integers.  Every
+// value of the column lies below 2^E (or E is kNonFinite), so the right
+// shift to units of 2^(E - 24) is t = E + 126 - eb >= 0 and the rounding
+// (((2 m) >> t) + 1) >> 1 (ties up) stays within 32 bits; t >= 25 gives 0.
 __device__ __forceinline__ long long biased_value_f32(float x, int E) {
     const unsigned int bits = __float_as_uint(x);
     const int eb = (int)((bits >> 23) & 0xFF);
-    int v = 0;
-    if (eb != 0 && eb != 0xFF && E < kNonFinite) {
-        const int m = (int)((bits & 0x7FFFFF) | 0x800000);
-        const int shift = (eb - 150) + 24 - E;
-        if (shift >= 0)
-            v = m << shift;
-        else if (shift > -31)
-            v = (int)(((long long)m + (1LL << (-shift - 1))) >> (-shift));
-        if (bits >> 31) v = -v;
-    }
-    return (long long)(v + 0x8080);
+    const unsigned int m2 = ((bits & 0x7FFFFFu) | 0x800000u) << 1;
+    unsigned int v = ((m2 >> min((unsigned int)(E + 126 - eb), 31u)) + 1u) >> 1;
+    if (eb == 0) v = 0;
+    return (long long)(((bits >> 31) ? -(int)v : (int)v) + 0x8080);
 }
 
 // FP32 bits of (b - 128) * 2^-8(s+1) for biased digit b = b[s] of u, in

@@ -675,7 +675,9 @@ __device__ __forceinline__ void load_operand_tile(const BindSet<NB>& bs, const T
 // reduced in registers over a thread's rows, then across the threads of a
 // column; one atomic per column and block.
 template <typename TS>
-__device__ __forceinline__ unsigned long long abs_bits(TS x) {
+using AbsBits = std::conditional_t<sizeof(TS) == 8, unsigned long long, unsigned int>;
+template <typename TS>
+__device__ __forceinline__ AbsBits<TS> abs_bits(TS x) {
     if constexpr (sizeof(TS) == 8)
         return (unsigned long long)__double_as_longlong((double)x) & 0x7FFFFFFFFFFFFFFFull;
     else
@@ -692,12 +694,13 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
                                                         const TcProd* __restrict__ tcp,
                                                         const PrepTask* __restrict__ tasks) {
     using TR = TileRegs<TS>;
+    using MB = AbsBits<TS>;  // magnitude bits: 32-bit compares for FP32 values
     constexpr int NRED = 256 / TR::VPR;  // threads sharing a column vector
-    __shared__ unsigned long long red[NRED][PT];
+    __shared__ MB red[NRED][PT];
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
-    unsigned long long m[TR::VEC];
+    MB m[TR::VEC];
 #pragma unroll
     for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
     // magnitudes compared as bit patterns (integer operations only)
@@ -706,8 +709,8 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
         for (int j = 0; j < TR::VEC; ++j)
 #pragma unroll
             for (int p = 0; p < TR::NPASS; ++p) {
-                const unsigned long long b0 = abs_bits(x0[p][j]), b1 = abs_bits(x1[p][j]);
-                const unsigned long long b = b0 > b1 ? b0 : b1;
+                const MB b0 = abs_bits(x0[p][j]), b1 = abs_bits(x1[p][j]);
+                const MB b = b0 > b1 ? b0 : b1;
                 m[j] = b > m[j] ? b : m[j];
             }
     };
@@ -736,11 +739,12 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
     __syncthreads();
     if (threadIdx.x < PT) {
         const int col = threadIdx.x;
-        unsigned long long mx = red[0][col];
+        MB mb = red[0][col];
 #pragma unroll
-        for (int i = 1; i < NRED; ++i) mx = red[i][col] > mx ? red[i][col] : mx;
-        if (mx != 0) {
-            if constexpr (sizeof(TS) == 4) mx = (unsigned long long)__double_as_longlong((double)__uint_as_float((unsigned)mx));
+        for (int i = 1; i < NRED; ++i) mb = red[i][col] > mb ? red[i][col] : mb;
+        if (mb != 0) {
+            unsigned long long mx = mb;
+            if constexpr (sizeof(TS) == 4) mx = (unsigned long long)__double_as_longlong((double)__uint_as_float(mb));
             unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
             atomicMax(ex + tk.c0 + col, mx);
         }
@@ -784,13 +788,13 @@ __device__ __forceinline__ long long biased_value(long long v) {
 // value of the column lies below 2^E (or E is kNonFinite), so the right
 // shift to units of 2^(E - 24) is t = E + 126 - eb >= 0 and the rounding
 // (((2 m) >> t) + 1) >> 1 (ties up) stays within 32 bits; t >= 25 gives 0.
-__device__ __forceinline__ long long biased_value_f32(float x, int E) {
+__device__ __forceinline__ int biased_value_f32(float x, int E) {
     const unsigned int bits = __float_as_uint(x);
     const int eb = (int)((bits >> 23) & 0xFF);
     const unsigned int m2 = ((bits & 0x7FFFFFu) | 0x800000u) << 1;
     unsigned int v = ((m2 >> min((unsigned int)(E + 126 - eb), 31u)) + 1u) >> 1;
     if (eb == 0) v = 0;
-    return (long long)(((bits >> 31) ? -(int)v : (int)v) + 0x8080);
+    return ((bits >> 31) ? -(int)v : (int)v) + 0x8080;
 }
 
 // FP32 bits of (b - 128) * 2^-8(s+1) for biased digit b = b[s] of u, in
@@ -805,8 +809,8 @@ __host__ __device__ constexpr float exp2_neg(int e) {
     return r;
 }
 
-template <int S, int s>
-__device__ __forceinline__ uint32_t digit_f32_bits(long long u) {
+template <int S, int s, typename U>
+__device__ __forceinline__ uint32_t digit_f32_bits(U u) {
     constexpr float scale = exp2_neg(8 * (s + 1));
     uint32_t fb;
     if constexpr (s == 0) {
@@ -835,10 +839,10 @@ struct PrepSrc<MODE_OZAKI> {
 };
 
 // Writes the S parts of 8 consecutive K values of one column (their biased
-// values u): part s gets the 8 bf16 of digit s, 16 bytes at
-// out + s * part_elems + base.
-template <int S, int s = 0>
-__device__ __forceinline__ void store_parts(const long long (&u)[8], __nv_bfloat16* out, int64_t part_elems,
+// values u, 32-bit integers for S <= 3): part s gets the 8 bf16 of digit s,
+// 16 bytes at out + s * part_elems + base.
+template <int S, int s = 0, typename U>
+__device__ __forceinline__ void store_parts(const U (&u)[8], __nv_bfloat16* out, int64_t part_elems,
                                             int64_t base) {
     uint4 q;
     q.x = pack_bf16_hi(digit_f32_bits<S, s>(u[0]), digit_f32_bits<S, s>(u[1]));
@@ -894,7 +898,7 @@ __global__ void __launch_bounds__(256, 6) tc_prep_kernel(const __grid_constant__
             const unsigned long long mx =
                 reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
             const int E = col_exponent<Geo<MODE>::HEAD>(mx);
-            long long u[8];
+            std::conditional_t<sizeof(TS) == 8, long long, int> u[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 if constexpr (sizeof(TS) == 8)

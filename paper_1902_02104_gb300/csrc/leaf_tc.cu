@@ -11,13 +11,17 @@
 // Part products are exact in FP32.  The tensor core accumulates in FP32
 // with truncation, so an accumulator that runs over a long K drifts by a
 // relative ~2^-23 per addition.  Orders whose share of the result is large
-// are therefore accumulated per K chunk in their own accumulator, in which
-// every partial sum is an integer of at most 2^24 units, and drained
-// into float-float (hi, lo) sums by the epilogue after each chunk: orders 0-1
-// for bf16x3, 0-2 for ozaki.  The remaining orders (2 for bf16x3: ~2^-16 of
-// the result, accumulated over the whole K; 3-5 for ozaki, drained per chunk)
-// add errors far below the stated bounds.  Results are scaled back by
-// 2^(E_i + F_j) with integer exponent arithmetic and written in FP64.
+// are therefore accumulated per 256-deep K chunk in their own accumulator,
+// in which every partial sum is an integer of at most 2^24 units (exact):
+// order 0 for bf16x3, orders 0, 1 and 2 for ozaki.  The smaller orders share
+// one accumulator per chunk (bf16x3 orders 1-2, ~2^-8 of the result; ozaki
+// orders 3-5, ~2^-24, over 512-deep chunks) and add errors far below the
+// stated bounds.  After each chunk the epilogue adds the chunk sums to
+// running sums: ozaki into float-float (hi, lo) pairs that carry the FP64
+// result; bf16x3 adds the exact order-0 chunk to hi by TwoSum, its rounding
+// error kept in lo, and orders 1-2 straight into lo (an FP32-accurate result
+// needs no more).  Results are scaled back by 2^(E_i + F_j) with integer
+// exponent arithmetic and written in FP64.
 //
 // Stage 1 (operand preparation, memory bound): every leaf operand -- a signed
 // sum of blocks of A or of materialised Strassen sums -- is formed once,
@@ -1423,17 +1427,30 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                                     // most ~2^-8 of it), added to (hi, lo) as a float-float sum and
                                     // renormalised so that |lo| stays within half an ulp of hi;
                                     // two columns per instruction
-                                    f32x2 h, l, s2, e2;
-                                    two_sum2(pk2(__uint_as_float(a0[cc]), __uint_as_float(a0[cc + 1])),
-                                             pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1])), h, l);
-                                    if constexpr (G::ND > 2)
-                                        l = add2(l, pk2(__uint_as_float(a2[cc]), __uint_as_float(a2[cc + 1])));
                                     f32x2* lp = SH::LO_REGS ? &lo2r[(g * 16 + c) / 2] : lo2_s + ((col + c) / 2) * 128 + row;
-                                    two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]), h, s2, e2);
-                                    e2 = add2(e2, add2(lo_init ? *lp : 0ull, l));
-                                    const f32x2 hn = add2(s2, e2);  // Fast2Sum: |s2| >= |e2|
-                                    *lp = sub2(e2, sub2(hn, s2));
-                                    upk2(hn, hi[g * 16 + c], hi[g * 16 + c + 1]);
+                                    if constexpr (!G::FP64_SUM) {
+                                        // FP32-accuracy result: the exact order-0 chunk is added
+                                        // to hi with its rounding error kept (TwoSum), and the
+                                        // orders-1-2 chunk (about 2^-8 of it) goes straight into
+                                        // lo, whose FP32 rounding is then 2^-32 of the result
+                                        f32x2 s2, e2;
+                                        two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]),
+                                                 pk2(__uint_as_float(a0[cc]), __uint_as_float(a0[cc + 1])), s2, e2);
+                                        *lp = add2(lo_init ? *lp : 0ull,
+                                                   add2(e2, pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1]))));
+                                        upk2(s2, hi[g * 16 + c], hi[g * 16 + c + 1]);
+                                    } else {
+                                        f32x2 h, l, s2, e2;
+                                        two_sum2(pk2(__uint_as_float(a0[cc]), __uint_as_float(a0[cc + 1])),
+                                                 pk2(__uint_as_float(a1[cc]), __uint_as_float(a1[cc + 1])), h, l);
+                                        if constexpr (G::ND > 2)
+                                            l = add2(l, pk2(__uint_as_float(a2[cc]), __uint_as_float(a2[cc + 1])));
+                                        two_sum2(pk2(hi[g * 16 + c], hi[g * 16 + c + 1]), h, s2, e2);
+                                        e2 = add2(e2, add2(lo_init ? *lp : 0ull, l));
+                                        const f32x2 hn = add2(s2, e2);  // Fast2Sum: |s2| >= |e2|
+                                        *lp = sub2(e2, sub2(hn, s2));
+                                        upk2(hn, hi[g * 16 + c], hi[g * 16 + c + 1]);
+                                    }
                                 }
                             }
                         }

@@ -331,15 +331,25 @@ __device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&r)[8])
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Lanes' share of a thread's NCOL column exponents (at least one slot).
+template <typename G, int NCOL>
+struct SLICED_COLS {
+    static constexpr int W = G::SLICED && NCOL >= 32 ? NCOL / 32 : 1;
+};
+
 // Exact FP32 -> FP64 widening with integer operations (the FP64 pipe is the
-// scarce unit on this part); zero and subnormal inputs give 0, which changes
-// a result by less than 2^-126 of its unit; Inf and NaN stay Inf and NaN.
-__device__ __forceinline__ long long f2d_bits(float f) {
+// scarce unit on this part), scaled by 2^sc: the FP64 bits of f * 2^sc,
+// built in 32-bit halves (the high word takes the sign, the rebiased and
+// scaled exponent and the top 20 mantissa bits, the low word the last 3).
+// Zero and subnormal f give 0, which changes a result by less than 2^-126 of
+// its unit; an Inf or NaN f keeps its exponent.
+__device__ __forceinline__ long long f2d_scaled_bits(float f, int sc) {
     const unsigned int b = __float_as_uint(f);
     const unsigned int e = (b >> 23) & 0xFF;
     if (e == 0) return 0;
-    const long long eb = e == 0xFF ? 0x7FF : (long long)(e + 896);
-    return ((long long)(b >> 31) << 63) | (eb << 52) | ((long long)(b & 0x7FFFFF) << 29);
+    const unsigned int ex = e == 0xFF ? 0x7FFu : e + 896u + (unsigned int)sc;
+    const unsigned int hw = (b & 0x80000000u) | (ex << 20) | ((b >> 3) & 0xFFFFFu);
+    return (long long)(((unsigned long long)hw << 32) | (unsigned long long)(b << 29));
 }
 
 // Scale exponent E of a column whose largest magnitude has bit pattern mx:
@@ -1524,6 +1534,14 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                             (int64_t)i * pr->out_ld;
             const int64_t gi = (int64_t)pr->ci0 + i;
             double* prow = bind.C + (packed_start(gi, bind.n) - gi + p_cj0);
+            // column exponents: lane l takes those of columns j0 + 32 w + l,
+            // and every lane reads the ones it needs from the lane that holds
+            // them (one shuffle per entry instead of a load and a decode)
+            int Ecol[SLICED_COLS<G, NCOL>::W];
+            if constexpr (G::SLICED) {
+#pragma unroll
+                for (int w = 0; w < NCOL / 32; ++w) Ecol[w] = col_exponent<G::HEAD>(__ldg(p_ey + j0 + 32 * w + lane));
+            }
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const uint32_t col = cq * NCOL + g * 16;
@@ -1533,6 +1551,12 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                 } else {
 #pragma unroll
                     for (int c = 0; c < 16; ++c) f[c] = 0.f;
+                }
+                int Ej[16];
+                if constexpr (G::SLICED) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        Ej[c] = __shfl_sync(0xffffffffu, Ecol[(g * 16 + c) >> 5], (g * 16 + c) & 31);
                 }
                 if (row_ok) {
                     const bool dense_out = p_out_kind == OUT_DENSE || p_out_kind == OUT_CDENSE;
@@ -1560,13 +1584,8 @@ __global__ void __launch_bounds__(Shape<MODE, CG, NB>::THREADS, 1)
                                 hh += ll;
                                 ll = 0.f;
                             }
-                            long long bh = f2d_bits(hh), bl = f2d_bits(ll);
-                            int sc = 0;
-                            if constexpr (G::SLICED) {
-                                sc = Ei + col_exponent<G::HEAD>(__ldg(p_ey + j));
-                                if (bh) bh += (long long)sc << 52;
-                                if (bl) bl += (long long)sc << 52;
-                            }
+                            const int sc = G::SLICED ? Ei + Ej[c] : 0;
+                            const long long bh = f2d_scaled_bits(hh, sc), bl = f2d_scaled_bits(ll, sc);
                             if (G::SLICED && sc >= kNonFinite)
                                 v[q] = __longlong_as_double(0x7FF8000000000000LL);
                             else if constexpr (G::FP64_SUM)

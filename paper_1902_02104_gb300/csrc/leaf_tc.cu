@@ -714,6 +714,8 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
+    // where the block's maxima go, read before the tiles
+    unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
     MB m[TR::VEC];
 #pragma unroll
     for (int j = 0; j < TR::VEC; ++j) m[j] = 0;
@@ -759,7 +761,6 @@ __global__ void __launch_bounds__(256, 4) tc_colmax_kernel(const __grid_constant
         if (mb != 0) {
             unsigned long long mx = mb;
             if constexpr (sizeof(TS) == 4) mx = (unsigned long long)__double_as_longlong((double)__uint_as_float(mb));
-            unsigned long long* ex = reinterpret_cast<unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
             atomicMax(ex + tk.c0 + col, mx);
         }
     }
@@ -884,18 +885,22 @@ __global__ void __launch_bounds__(256, 6) tc_prep_kernel(const __grid_constant__
     const PrepTask tk = tasks[blockIdx.x];
     const LeafProduct& lp = prods[tk.prod];
     const int t0 = tk.side ? lp.y0 : lp.x0, nt = tk.side ? lp.ny : lp.nx;
+    // where the slices go and where the column scales are, read before the
+    // tile, so that these loads wait together with the tile's instead of
+    // after the barrier
+    const int rows_pad = tk.side ? lp.r_pad : lp.p_pad, K_pad = lp.K_pad;
+    char* parts = bs.b[lp.inst].W + (tk.side ? lp.tc_y_off : lp.tc_x_off);
+    const unsigned long long* ex =
+        reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex);
     load_operand_tile<TS>(bs, terms, t0, nt, lp.K, tk.k0, tk.c0, tile);
     __syncthreads();
-    const int rows_pad = tk.side ? lp.r_pad : lp.p_pad;
-    const Bind& b = bs.b[lp.inst];
-    char* parts = b.W + (tk.side ? lp.tc_y_off : lp.tc_x_off);
-    const int64_t part_elems = (int64_t)rows_pad * lp.K_pad;
+    const int64_t part_elems = (int64_t)rows_pad * K_pad;
 #pragma unroll
     for (int rep = 0; rep < 2; ++rep) {
         const int item = threadIdx.x + rep * 256;
         const int col = item >> 3, kc = item & 7;
         const int c = tk.c0 + col;
-        const int64_t base = (int64_t)c * lp.K_pad + tk.k0 + kc * 8;
+        const int64_t base = (int64_t)c * K_pad + tk.k0 + kc * 8;
         if constexpr (MODE == MODE_TF32) {
             float v[8];
 #pragma unroll
@@ -909,9 +914,7 @@ __global__ void __launch_bounds__(256, 6) tc_prep_kernel(const __grid_constant__
             *reinterpret_cast<uint4*>(out + base + 4) = *reinterpret_cast<const uint4*>(v + 4);
         } else {
             constexpr int S = Geo<MODE>::PARTS;
-            const unsigned long long mx =
-                reinterpret_cast<const unsigned long long*>(tk.side ? tcp[tk.prod].ey : tcp[tk.prod].ex)[c];
-            const int E = col_exponent<Geo<MODE>::HEAD>(mx);
+            const int E = col_exponent<Geo<MODE>::HEAD>(__ldg(ex + c));
             std::conditional_t<sizeof(TS) == 8, long long, int> u[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {

@@ -248,6 +248,19 @@ def test_ozaki_worst_case_bound(gpu, gen):
 
 
 # ---------------------------------------------------------------------------
+# The bf16x3 running sum: every 256-deep chunk's order-0 sum joins hi
+# exactly (TwoSum) and its orders-1-2 sum goes straight into the low part.
+# Over K = 2^17 (512 chunks) with every product positive, that low part and
+# its rounding grow the most; each entry must still be within a few units of
+# 2^-24 (FP32 accuracy) of the exact product.
+
+def test_bf16x3_long_k_same_sign_componentwise(gpu):
+    A = np.abs(inputs.uniform(131072, 96, seed=11, dtype=np.float32))
+    C, _ = run(A, ata.ATA_F32_BF16X3, 4096)
+    err = oracle.componentwise_error(C, oracle.ata_packed(A), oracle.abs_gram_packed(A))
+    assert err <= 2.5e-7, err
+
+
 # Winograd's variant in the FP32 modes, at the precision form's bounds
 
 @pytest.mark.parametrize("dtype", MODES32)

@@ -104,7 +104,7 @@ def tensor_peak(mode):
 LEAF_TRAFFIC = {
     # a one-launch capture of the 4500^2 small case (cutoff 1200), scaled by
     # the ratio of tree multiplications (traffic grows with tiles x K)
-    ("ata_ozaki_10000x10000", "3414e54caf71f7c5"): (939.5e6 + 95.8e6) * 468800000000 / 42724968750,
+    ("ata_ozaki_10000x10000", "c9d903142d171577"): (940.4e6 + 95.2e6) * 468800000000 / 42724968750,
 }
 
 

@@ -69,10 +69,14 @@ typedef enum {
 typedef enum {
     ATA_F64 = 0,           /* FP64 input, FP64 leaves (DFMA), FP64 sums       */
     ATA_F32_BF16X3 = 1,    /* FP32 input, leaves on bf16 tensor cores with a
-                              3-way split of each operand, FP32 accumulation
-                              in chunks added into FP64                      */
-    ATA_F32_TF32 = 2,      /* FP32 input, TF32 tensor-core leaves, FP32
-                              accumulation in chunks added into FP64          */
+                              3-way split of each operand; the leading part
+                              products are summed exactly per 256-deep K
+                              chunk, the chunks added into a pair of FP32
+                              values, and the result written in FP64;
+                              normwise error <= 1e-6                          */
+    ATA_F32_TF32 = 2,      /* FP32 input rounded to TF32, tensor-core leaves
+                              accumulating in FP32 over the whole K, the
+                              result written in FP64; normwise error <= 1e-3 */
     ATA_F64_OZAKI = 3      /* FP64 input, FP64-accuracy leaves emulated on
                               bf16 tensor cores (exact slice products, FP64
                               Strassen sums and final accumulation).  Each
